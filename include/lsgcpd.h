@@ -1,0 +1,182 @@
+/*
+ * lsgcpd.h -- C ABI of the GB300 (sm_103a) implementation of LSG-CPD:
+ * "Coherent Point Drift with Local Surface Geometry for Point Cloud
+ * Registration" (Liu, Wu, Chirikjian, ICCV 2021).
+ *
+ * Problem (Sec. 3.1): fix a target cloud Y (M points), align a source cloud X
+ * (N points) by a rigid motion g = (R, t), maximising the likelihood of the
+ * Gaussian mixture of Eq. (1) built on the target with the anisotropic
+ * components of Eq. (2) and a uniform outlier term.  EM (Sec. 3.1): E step of
+ * Eq. (5) / Eq. (9); M step by Newton on SE(3) (Eqs. (11)-(13)) and the
+ * sigma^2 update.
+ *
+ * Conventions for every entry point:
+ *  - Return value: an lsgcpd_status.  Nothing aborts or traps; on error the
+ *    message is available from lsgcpd_last_error(ctx).
+ *  - Point arrays are row-major N x 3 (or M x 3) FP32.  Unless stated
+ *    otherwise they are DEVICE pointers on the context's device.
+ *  - The caller owns every array passed in; the context owns all scratch
+ *    memory, CUDA graphs and events.  Entry points never free caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls that return host values synchronise that stream.
+ *  - A context serves one call at a time (not thread-safe).
+ *  - Rotations are row-major 3x3 doubles, translations 3 doubles, in the
+ *    caller's (uncentred) frame: y ~ R x + t.
+ */
+#ifndef LSGCPD_H_
+#define LSGCPD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsgcpd_ctx lsgcpd_ctx;
+
+typedef enum {
+  LSGCPD_OK = 0,
+  LSGCPD_EINVAL = 1,   /* invalid argument (size, range, NaN/Inf, null pointer) */
+  LSGCPD_ENOMEM = 2,   /* device allocation failed or above the context capacity */
+  LSGCPD_ECUDA = 3,    /* a CUDA runtime call failed */
+  LSGCPD_ETIMEOUT = 4, /* a bounded device wait expired; results are invalid */
+  LSGCPD_ENUMERIC = 5  /* the posterior mass vanished (all sources outliers) */
+} lsgcpd_status;
+
+/* Per-iteration trace record (lsgcpd_register):
+ * sigma2 (after the update), N_P = sum P, Q_d(g_new), Newton steps, damped
+ * steps, motion of the iteration (max(rotation angle, |dt| / diag)),
+ * negative log-likelihood of Eq. (4) at the E step, outlier mass sum P_out. */
+#define LSGCPD_TRACE_WIDTH 8
+
+/* Per-source E-step output width (lsgcpd_estep `per_n`, see there). */
+#define LSGCPD_PER_N_WIDTH 16
+
+/* Global E-step moments returned by lsgcpd_estep (doubles):
+ *   [0]      N_P = sum_n Pbar_n
+ *   [1]      sum_n D_n
+ *   [2..13]  H1 (3x4 row-major) = sum_n h_n xt_n^T,  h_n = rho_n + beta_n
+ *   [14..73] G = sum_n A_n (x) xt_n xt_n^T, A_n = Pbar_n I + W_n, 60 unique
+ *            entries ordered by A pair (00,01,02,11,12,22) major and
+ *            xt pair (00,01,02,03,11,12,13,22,23,33) minor
+ *   [74]     sum_n Pout_n
+ *   [75]     sum_n -log p(z_n) (Eq. (4)) at (R, t, sigma2)
+ * with xt_n = [x_n; 1] in the caller's frame.  Per-source moments are
+ * defined under lsgcpd_estep. */
+#define LSGCPD_MOMENTS 76
+
+typedef struct {
+  double w;           /* outlier weight w0 in [0, 1) of Eq. (1); uniform w_n = w          */
+  double alpha_max;   /* upper bound of the penalty, Eq. (3)                               */
+  double lambda;      /* sensitivity of the penalty, Eq. (3)                               */
+  double tol;         /* EM stops when an iteration moves less than tol; 0 = never         */
+  double volume;      /* V of p_o = 1/V; <= 0 -> target AABB volume, sides >= 1e-2 diag   */
+  double sigma2_init; /* <= 0 -> CPD start sum |g0 x_n - y_m|^2 / (3 N M)                  */
+  double init_R[9];   /* initial g0 (identity by default); resuming = passing a prior g   */
+  double init_t[3];
+  double newton_tol;  /* inner Newton stop on |xi| (default 1e-12)                         */
+  double sigma2_floor_rel; /* sigma^2 floor relative to diag^2 (default 1e-10); hitting it ends EM */
+  int32_t knn_k;      /* neighbourhood size for normals and surface variation (default 10) */
+  int32_t max_iters;  /* EM iterations (default 50)                                        */
+  int32_t include_alpha_norm; /* 0: Eq. (9) as printed; 1: component constant with sqrt(1+alpha) */
+  int32_t newton_max; /* inner Newton steps per M step (default 20)                       */
+  int32_t precision;  /* 0: FP32 E step (the only mode implemented; others -> EINVAL)     */
+  int32_t reserved;
+} lsgcpd_params;
+
+/* Result of a registration (host struct filled by lsgcpd_register). */
+typedef struct {
+  double R[9];
+  double t[3];
+  double sigma2;
+  int32_t iters;      /* EM iterations run */
+  int32_t mode;       /* 0: fixed outlier shift, 1: per-source max shift (w = 0 or extreme V) */
+  double ms_estep;    /* device time of the E-step kernels (only with timing enabled) */
+  double ms_total;    /* device time of the whole call (only with timing enabled)     */
+} lsgcpd_result;
+
+/* Fill *p with the defaults: w 0.1, alpha_max 2, lambda 0.2, tol 0, volume 0,
+ * sigma2_init 0, identity g0, newton_tol 1e-12, floor 1e-10, k 10, 50
+ * iterations, Eq. (9) constant, 20 Newton steps, FP32. */
+void lsgcpd_params_default(lsgcpd_params* p);
+
+/* Create a context on `device` able to handle up to max_N sources and max_M
+ * targets (both >= 1).  Allocates all scratch memory up front; later calls
+ * allocate nothing unless a larger size is requested.  *out is set on success. */
+lsgcpd_status lsgcpd_create(lsgcpd_ctx** out, int device, int64_t max_N, int64_t max_M);
+
+/* Release every resource of the context (NULL is ignored). */
+void lsgcpd_destroy(lsgcpd_ctx* ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" after success). */
+const char* lsgcpd_last_error(const lsgcpd_ctx* ctx);
+
+/* Enable (1) or disable (0) device timing with CUDA events; results appear in
+ * lsgcpd_result.ms_* and lsgcpd_last_timing(). */
+lsgcpd_status lsgcpd_set_timing(lsgcpd_ctx* ctx, int enable);
+
+/* Device times (ms) of the last call: [0] total, [1] E-step kernels, [2]
+ * combine kernels, [3] M-step kernels, [4] preprocessing; [5] number of
+ * E-step launches timed.  Returns EINVAL if timing is off. */
+lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* ctx, double out[6]);
+
+/* Local surface geometry of the target (Sec. 3.1, Eqs. (2)-(3)): for every
+ * target m, its k nearest targets (self included, ties to the lower index,
+ * FP32 squared distances), the neighbourhood covariance about its mean, the
+ * smallest eigenpair (FP64 Jacobi), the surface variation
+ * kappa_m = lambda_min / trace in [0, 1/3] and the penalty
+ * alpha_m = alpha_max tanh(lambda (1/kappa_m - 3) / 2) of Eq. (3).
+ *   Y       device, M x 3 FP32 (input)
+ *   normals device, M x 3 FP32 (output, unit; the sign is arbitrary) or NULL
+ *   kappa   device, M FP32 (output) or NULL
+ *   alpha   device, M FP32 (output) or NULL
+ *   knn_idx device, M x k int32 (output, ascending distance) or NULL
+ * Uses p->knn_k, p->alpha_max, p->lambda.  Requires 1 <= k <= min(M, 32). */
+lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* ctx, const float* Y, int64_t M, const lsgcpd_params* p,
+                                float* normals, float* kappa, float* alpha, int32_t* knn_idx,
+                                void* stream);
+
+/* One E step (Eq. (5), computed as Eq. (9) with gamma_n = w/(1-w) (2 pi s2)^{3/2} / V)
+ * at z_n = R x_n + t for the given target geometry, followed by the per-source
+ * normalisation and the FP64 moment reduction consumed by the M step.
+ *   X       device, N x 3 FP32 sources;  Y, normals (unit), alpha: device, target side
+ *   R, t    host, the pose at which the posteriors are evaluated
+ *   sigma2  > 0;  volume > 0 (V of p_o = 1/V)
+ *   moments host, LSGCPD_MOMENTS doubles (output) or NULL
+ *   per_n   device, N x LSGCPD_PER_N_WIDTH FP32 (output) or NULL, per source n:
+ *           [0] Pbar = sum_m P_mn, [1..3] rho = sum_m P_mn r_mn (r = z_n - y_m),
+ *           [4..9] W = sum_m P_mn alpha_m n_m n_m^T (00,01,02,11,12,22),
+ *           [10..12] beta = sum_m P_mn alpha_m (n_m . r_mn) n_m,
+ *           [13] D = sum_m P_mn d_mn, d = |r|^2 + alpha (n . r)^2, [14] Pout, [15] 0.
+ * Uses p->w (0 allowed: no outlier term) and p->include_alpha_norm. */
+lsgcpd_status lsgcpd_estep(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y,
+                           const float* normals, const float* alpha, int64_t M,
+                           const lsgcpd_params* p, const double R[9], const double t[3],
+                           double sigma2, double volume, double* moments, float* per_n,
+                           void* stream);
+
+/* M step from the global moments of one E step (Eqs. (11)-(13) and the
+ * sigma^2 update): Newton on SE(3) with the posteriors fixed, starting at
+ * (R, t), with the damping / halving rules of the parameter block; then
+ * sigma2 = Q_d(g_new) / (3 N_P) (no floor).  All arguments are host memory.
+ * info (4 int32, may be NULL): Newton steps, damped steps, halvings, 0. */
+lsgcpd_status lsgcpd_mstep(lsgcpd_ctx* ctx, const double* moments, const double R[9],
+                           const double t[3], const lsgcpd_params* p, double R_out[9],
+                           double t_out[3], double* sigma2_out, int32_t* info, void* stream);
+
+/* Full registration: preprocessing of the target, initial sigma^2 and V,
+ * then p->max_iters EM iterations (E step, moment reduction, Newton M step,
+ * sigma^2 update) captured once per problem shape in a CUDA graph and
+ * replayed.  X and Y may be HOST or DEVICE pointers (detected per pointer);
+ * host inputs are copied into the context.  out receives the result in the
+ * caller's frame.  trace (host, max_iters x LSGCPD_TRACE_WIDTH doubles) may be
+ * NULL.  Returns ENUMERIC if the posterior mass vanished (result = last pose). */
+lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y, int64_t M,
+                              const lsgcpd_params* p, lsgcpd_result* out, double* trace,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSGCPD_H_ */

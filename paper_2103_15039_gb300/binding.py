@@ -1,0 +1,278 @@
+"""Thin ctypes binding of liblsgcpd (include/lsgcpd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Functions carry the C names; ``Context`` bundles them for convenience.  Device
+arrays are torch CUDA tensors (float32, contiguous); host arrays may be numpy
+arrays or CPU tensors (``lsgcpd_register`` accepts either for X and Y).
+There is no CPU fallback: if the library cannot be built or loaded, the first
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+MOMENTS = 76
+TRACE_WIDTH = 8
+PER_N_WIDTH = 16
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUMERIC"}
+
+
+class LsgcpdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("w", C.c_double), ("alpha_max", C.c_double), ("lam", C.c_double), ("tol", C.c_double),
+        ("volume", C.c_double), ("sigma2_init", C.c_double), ("init_R", C.c_double * 9),
+        ("init_t", C.c_double * 3), ("newton_tol", C.c_double), ("sigma2_floor_rel", C.c_double),
+        ("knn_k", C.c_int32), ("max_iters", C.c_int32), ("include_alpha_norm", C.c_int32),
+        ("newton_max", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("sigma2", C.c_double),
+                ("iters", C.c_int32), ("mode", C.c_int32), ("ms_estep", C.c_double),
+                ("ms_total", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, dp, fp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p
+        i64 = C.c_int64
+        L.lsgcpd_params_default.argtypes = [C.POINTER(Params)]
+        L.lsgcpd_params_default.restype = None
+        L.lsgcpd_create.argtypes = [C.POINTER(vp), C.c_int, i64, i64]
+        L.lsgcpd_create.restype = C.c_int
+        L.lsgcpd_destroy.argtypes = [vp]
+        L.lsgcpd_destroy.restype = None
+        L.lsgcpd_last_error.argtypes = [vp]
+        L.lsgcpd_last_error.restype = C.c_char_p
+        L.lsgcpd_set_timing.argtypes = [vp, C.c_int]
+        L.lsgcpd_set_timing.restype = C.c_int
+        L.lsgcpd_last_timing.argtypes = [vp, dp]
+        L.lsgcpd_last_timing.restype = C.c_int
+        L.lsgcpd_preprocess.argtypes = [vp, fp, i64, C.POINTER(Params), fp, fp, fp, ip, vp]
+        L.lsgcpd_preprocess.restype = C.c_int
+        L.lsgcpd_estep.argtypes = [vp, fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
+                                   C.c_double, dp, fp, vp]
+        L.lsgcpd_estep.restype = C.c_int
+        L.lsgcpd_mstep.argtypes = [vp, dp, dp, dp, C.POINTER(Params), dp, dp, dp, C.POINTER(C.c_int32), vp]
+        L.lsgcpd_mstep.restype = C.c_int
+        L.lsgcpd_register.argtypes = [vp, fp, i64, fp, i64, C.POINTER(Params), C.POINTER(Result), dp, vp]
+        L.lsgcpd_register.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def library_path():
+    return os.path.abspath(_build.LIB)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().lsgcpd_params_default(C.byref(p))
+    for key, val in kw.items():
+        if key in ("init_R", "init_t"):
+            arr = np.asarray(val, dtype=np.float64).ravel()
+            dst = getattr(p, key)
+            for i, v in enumerate(arr):
+                dst[i] = float(v)
+        elif key == "lambda":
+            p.lam = float(val)
+        else:
+            setattr(p, key, val)
+    return p
+
+
+def _dev_ptr(t, name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 and t.dtype != torch.int32:
+        raise TypeError(f"{name} must be float32 (or int32 for indices)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _any_ptr(a, name):
+    """Pointer to a float32 N x 3 array on host (numpy / CPU tensor) or device (CUDA tensor)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous() or a.dim() != 2 or a.shape[1] != 3:
+                raise ValueError(f"{name} must be a contiguous float32 n x 3 tensor")
+            return C.c_void_p(a.data_ptr()), a.shape[0], a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    if arr.ndim != 2 or arr.shape[1] != 3:
+        raise ValueError(f"{name} must be n x 3")
+    return C.c_void_p(arr.ctypes.data), arr.shape[0], arr
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _d(arr, n):
+    a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).ravel())
+    if a.size != n:
+        raise ValueError(f"expected {n} values")
+    return a
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        msg = lib().lsgcpd_last_error(ctx).decode(errors="replace")
+        raise LsgcpdError(rc, msg)
+
+
+def lsgcpd_create(device=0, max_N=1, max_M=1):
+    h = C.c_void_p()
+    rc = lib().lsgcpd_create(C.byref(h), int(device), int(max_N), int(max_M))
+    if rc != 0:
+        raise LsgcpdError(rc, "lsgcpd_create failed")
+    return h
+
+
+def lsgcpd_destroy(ctx):
+    lib().lsgcpd_destroy(ctx)
+
+
+def lsgcpd_preprocess(ctx, Y, params, want_idx=False, stream=None):
+    import torch
+    M = Y.shape[0]
+    _dev_ptr(Y, "Y", (M, 3))
+    dev = Y.device
+    normals = torch.empty((M, 3), dtype=torch.float32, device=dev)
+    kappa = torch.empty(M, dtype=torch.float32, device=dev)
+    alpha = torch.empty(M, dtype=torch.float32, device=dev)
+    idx = torch.empty((M, params.knn_k), dtype=torch.int32, device=dev) if want_idx else None
+    rc = lib().lsgcpd_preprocess(ctx, C.c_void_p(Y.data_ptr()), M, C.byref(params),
+                                 C.c_void_p(normals.data_ptr()), C.c_void_p(kappa.data_ptr()),
+                                 C.c_void_p(alpha.data_ptr()),
+                                 C.c_void_p(idx.data_ptr()) if idx is not None else None, _stream(stream))
+    _check(ctx, rc)
+    return dict(normals=normals, kappa=kappa, alpha=alpha, idx=idx)
+
+
+def lsgcpd_estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None):
+    import torch
+    N, M = X.shape[0], Y.shape[0]
+    _dev_ptr(X, "X", (N, 3))
+    _dev_ptr(Y, "Y", (M, 3))
+    _dev_ptr(normals, "normals", (M, 3))
+    _dev_ptr(alpha, "alpha", (M,))
+    Rd, td = _d(R, 9), _d(t, 3)
+    mom = np.zeros(MOMENTS)
+    pn = torch.empty((N, PER_N_WIDTH), dtype=torch.float32, device=X.device) if per_n else None
+    dpp = C.POINTER(C.c_double)
+    rc = lib().lsgcpd_estep(ctx, C.c_void_p(X.data_ptr()), N, C.c_void_p(Y.data_ptr()),
+                            C.c_void_p(normals.data_ptr()), C.c_void_p(alpha.data_ptr()), M,
+                            C.byref(params), Rd.ctypes.data_as(dpp), td.ctypes.data_as(dpp), float(sigma2),
+                            float(volume), mom.ctypes.data_as(dpp),
+                            C.c_void_p(pn.data_ptr()) if pn is not None else None, _stream(stream))
+    _check(ctx, rc)
+    return dict(moments=mom, per_n=pn)
+
+
+def lsgcpd_mstep(ctx, moments, R, t, params, stream=None):
+    m = _d(moments, MOMENTS)
+    Rd, td = _d(R, 9), _d(t, 3)
+    Ro = np.zeros(9)
+    to = np.zeros(3)
+    s2 = C.c_double(0)
+    info = (C.c_int32 * 4)()
+    dpp = C.POINTER(C.c_double)
+    rc = lib().lsgcpd_mstep(ctx, m.ctypes.data_as(dpp), Rd.ctypes.data_as(dpp), td.ctypes.data_as(dpp),
+                            C.byref(params), Ro.ctypes.data_as(dpp), to.ctypes.data_as(dpp), C.byref(s2),
+                            info, _stream(stream))
+    _check(ctx, rc)
+    return dict(R=Ro.reshape(3, 3), t=to, sigma2=s2.value, newton_iters=info[0], damped=info[1],
+                halvings=info[2])
+
+
+def lsgcpd_register(ctx, X, Y, params, trace=False, stream=None):
+    xp, N, _xk = _any_ptr(X, "X")
+    yp, M, _yk = _any_ptr(Y, "Y")
+    res = Result()
+    tr = np.zeros((max(params.max_iters, 1), TRACE_WIDTH)) if trace else None
+    rc = lib().lsgcpd_register(ctx, xp, N, yp, M, C.byref(params), C.byref(res),
+                               tr.ctypes.data_as(C.POINTER(C.c_double)) if tr is not None else None,
+                               _stream(stream))
+    _check(ctx, rc)
+    out = dict(R=np.array(res.R[:]).reshape(3, 3), t=np.array(res.t[:]), sigma2=res.sigma2,
+               iters=res.iters, mode=res.mode, ms_estep=res.ms_estep, ms_total=res.ms_total)
+    if tr is not None:
+        out["trace"] = tr[: res.iters]
+    return out
+
+
+def lsgcpd_set_timing(ctx, enable):
+    lib().lsgcpd_set_timing(ctx, 1 if enable else 0)
+
+
+def lsgcpd_last_timing(ctx):
+    out = np.zeros(6)
+    lib().lsgcpd_last_timing(ctx, out.ctypes.data_as(C.POINTER(C.c_double)))
+    return dict(ms_total=out[0], ms_estep=out[1], ms_combine=out[2], ms_mstep=out[3], ms_prep=out[4],
+                launches=int(out[5]))
+
+
+class Context:
+    """One device context of the library (scratch memory, graphs, events)."""
+
+    def __init__(self, device=0, max_n=1, max_m=1):
+        self.handle = lsgcpd_create(device, max_n, max_m)
+
+    def close(self):
+        if self.handle:
+            lsgcpd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def preprocess(self, Y, params, want_idx=False, stream=None):
+        return lsgcpd_preprocess(self.handle, Y, params, want_idx, stream)
+
+    def estep(self, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None):
+        return lsgcpd_estep(self.handle, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n, stream)
+
+    def mstep(self, moments, R, t, params, stream=None):
+        return lsgcpd_mstep(self.handle, moments, R, t, params, stream)
+
+    def register(self, X, Y, params, trace=False, stream=None):
+        return lsgcpd_register(self.handle, X, Y, params, trace, stream)
+
+    def set_timing(self, enable):
+        lsgcpd_set_timing(self.handle, enable)
+
+    def last_timing(self):
+        return lsgcpd_last_timing(self.handle)

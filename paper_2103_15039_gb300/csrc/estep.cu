@@ -1,0 +1,570 @@
+// E step of LSG-CPD on sm_103a (Eq. (5) evaluated in the form of Eq. (9)).
+//
+// For every source n and every target m (Eq. (2)):
+//   r_mn = z_n - y_m,  d_mn = |r|^2 + alpha_m (n_m . r)^2 = |r|^2 + (a_m . r)^2,  a = sqrt(alpha) n
+//   P_mn = pi_m e^{-d/(2 s2)} / (sum_k pi_k e^{-d_k/(2 s2)} + gamma_n),
+//   gamma_n = w/(1-w) (2 pi s2)^{3/2} / V.
+// The kernel never forms P.  It evaluates e_mn = 2^(l_m - c d_mn - L_n) with
+// c = log2(e)/(2 s2) and a per-source shift L_n, and accumulates 14 per-source
+// moments (S0, rho, W, beta, D') from which the normalised posteriors'
+// sufficient statistics follow by one division (combine kernel below):
+//   S0 = sum e, rho = sum e r, W = sum e a a^T, beta = sum e (a.r) a,
+//   D' = sum e (d + kappa_n),  kappa_n = L_n / c.
+// Folding kappa_n into the squared distance makes the shift free in the hot
+// loop; the combine subtracts kappa_n S0 in FP64.
+//
+// Hot-loop layout (GB300):
+//  * a CTA = 4 warps; each thread owns S sources (z_n duplicated into both
+//    halves of an FP32x2 register) and 14 FP32x2 accumulators per source;
+//  * the two halves of every packed register belong to two consecutive
+//    targets, so every operation of the pair update is one packed
+//    FADD2/FMUL2/FFMA2 (26 per target pair per source) plus two MUFU.EX2;
+//  * target tiles (kTile records, 6.5 KB) stream into a 4-stage shared-memory
+//    ring by cp.async.bulk (TMA bulk copy) completing on mbarriers; every warp
+//    reads the tile with broadcast 128-bit shared loads;
+//  * work = (source block) x (target tile) units split stream-K style over a
+//    grid of (SM count x resident CTAs); a CTA flushes its FP32 partial
+//    moments at block boundaries and every seg_cap tiles, so FP32 sums stay
+//    short and the FP64 combine adds the pieces in a fixed order.
+// No tensor cores: the contraction depth is 3, so the work is FP32-pipe bound.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace lsg {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kNW = 4;  // warps per CTA of the hot kernel
+constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Arm the barrier for `bytes` of transaction and start a bulk copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after kWaitBudgetCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > kWaitBudgetCycles) return false;
+  }
+}
+
+struct Src {
+  float2 z0, z1, z2;  // z_n in both halves
+  float2 kp;          // kappa_n in both halves
+};
+
+struct Acc {
+  float2 s0, r0, r1, r2, w00, w01, w02, w11, w12, w22, b0, b1, b2, d;
+};
+
+struct Tgt {  // two consecutive targets, one per half
+  float2 ny0, ny1, ny2, a0, a1, a2, q00, q01, q02, q11, q12, q22, l;
+};
+
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+// One source against two targets: 26 packed FP32 operations and 2 EX2.
+__device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g, float2 nc) {
+  const float2 r0 = __fadd2_rn(s.z0, g.ny0);
+  const float2 r1 = __fadd2_rn(s.z1, g.ny1);
+  const float2 r2 = __fadd2_rn(s.z2, g.ny2);
+  float2 dd = __ffma2_rn(r2, r2, s.kp);
+  dd = __ffma2_rn(r1, r1, dd);
+  dd = __ffma2_rn(r0, r0, dd);
+  float2 v = __fmul2_rn(g.a0, r0);
+  v = __ffma2_rn(g.a1, r1, v);
+  v = __ffma2_rn(g.a2, r2, v);
+  dd = __ffma2_rn(v, v, dd);                 // d + kappa_n
+  const float2 x = __ffma2_rn(dd, nc, g.l);  // l_m - c (d + kappa_n)
+  float2 e;
+  e.x = ex2_approx(x.x);
+  e.y = ex2_approx(x.y);
+  A.s0 = __fadd2_rn(A.s0, e);
+  A.r0 = __ffma2_rn(e, r0, A.r0);
+  A.r1 = __ffma2_rn(e, r1, A.r1);
+  A.r2 = __ffma2_rn(e, r2, A.r2);
+  A.w00 = __ffma2_rn(e, g.q00, A.w00);
+  A.w01 = __ffma2_rn(e, g.q01, A.w01);
+  A.w02 = __ffma2_rn(e, g.q02, A.w02);
+  A.w11 = __ffma2_rn(e, g.q11, A.w11);
+  A.w12 = __ffma2_rn(e, g.q12, A.w12);
+  A.w22 = __ffma2_rn(e, g.q22, A.w22);
+  const float2 ev = __fmul2_rn(e, v);
+  A.b0 = __ffma2_rn(ev, g.a0, A.b0);
+  A.b1 = __ffma2_rn(ev, g.a1, A.b1);
+  A.b2 = __ffma2_rn(ev, g.a2, A.b2);
+  A.d = __ffma2_rn(e, dd, A.d);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int S>
+__device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)[S], Acc (&acc)[S],
+                                             float2 nc) {
+  const float4* T4 = reinterpret_cast<const float4*>(tile);
+  constexpr int Q = kTile / 4;
+#pragma unroll 1
+  for (int q = 0; q < Q; ++q) {
+    float4 P[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) P[p] = T4[p * Q + q];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      Tgt g;
+      g.ny0 = h ? hi2(P[0]) : lo2(P[0]);
+      g.ny1 = h ? hi2(P[1]) : lo2(P[1]);
+      g.ny2 = h ? hi2(P[2]) : lo2(P[2]);
+      g.a0 = h ? hi2(P[3]) : lo2(P[3]);
+      g.a1 = h ? hi2(P[4]) : lo2(P[4]);
+      g.a2 = h ? hi2(P[5]) : lo2(P[5]);
+      g.q00 = h ? hi2(P[6]) : lo2(P[6]);
+      g.q01 = h ? hi2(P[7]) : lo2(P[7]);
+      g.q02 = h ? hi2(P[8]) : lo2(P[8]);
+      g.q11 = h ? hi2(P[9]) : lo2(P[9]);
+      g.q12 = h ? hi2(P[10]) : lo2(P[10]);
+      g.q22 = h ? hi2(P[11]) : lo2(P[11]);
+      g.l = h ? hi2(P[12]) : lo2(P[12]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) pair_update(acc[s], src[s], g, nc);
+    }
+  }
+}
+
+__device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc& a) {
+  dst[0 * SB + nl] = a.s0.x + a.s0.y;
+  dst[1 * SB + nl] = a.r0.x + a.r0.y;
+  dst[2 * SB + nl] = a.r1.x + a.r1.y;
+  dst[3 * SB + nl] = a.r2.x + a.r2.y;
+  dst[4 * SB + nl] = a.w00.x + a.w00.y;
+  dst[5 * SB + nl] = a.w01.x + a.w01.y;
+  dst[6 * SB + nl] = a.w02.x + a.w02.y;
+  dst[7 * SB + nl] = a.w11.x + a.w11.y;
+  dst[8 * SB + nl] = a.w12.x + a.w12.y;
+  dst[9 * SB + nl] = a.w22.x + a.w22.y;
+  dst[10 * SB + nl] = a.b0.x + a.b0.y;
+  dst[11 * SB + nl] = a.b1.x + a.b1.y;
+  dst[12 * SB + nl] = a.b2.x + a.b2.y;
+  dst[13 * SB + nl] = a.d.x + a.d.y;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kNW * 32, (S >= 4 ? 2 : 3))
+    estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec,
+                 const EmState* __restrict__ st, const float* __restrict__ kap_n,
+                 float* __restrict__ part, int* __restrict__ status, int num_tiles,
+                 long long units, int seg_cap, int segs_max) {
+  constexpr int SB = kNW * 32 * S;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* tiles = reinterpret_cast<float*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kStages * kTileBytes);
+
+  if (st->done) return;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const long long G = gridDim.x;
+  const long long u0 = static_cast<long long>(blockIdx.x) * units / G;
+  const long long u1 = static_cast<long long>(blockIdx.x + 1) * units / G;
+  const int n_units = static_cast<int>(u1 - u0);
+  if (n_units <= 0) return;
+
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < kStages && i < n_units; ++i) {
+      const long long tile = (u0 + i) % num_tiles;
+      bulk_load(tiles + i * kTileFloats, rec + tile * kTileFloats, kTileBytes, &full[i]);
+    }
+  }
+
+  const float2 nc = dup(st->neg_c);
+  float Rm[9], tv[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Rm[i] = st->Rf[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) tv[i] = st->tf[i];
+  const float kap_uniform = st->kap;
+
+  bool abort = false;
+  int seg = 0;
+  int i = 0;  // units consumed by this CTA
+  long long u = u0;
+  while (u < u1) {
+    const int b = static_cast<int>(u / num_tiles);
+    const long long block_end = static_cast<long long>(b + 1) * num_tiles;
+    long long seg_end = u + seg_cap;
+    if (seg_end > block_end) seg_end = block_end;
+    if (seg_end > u1) seg_end = u1;
+
+    Src src[S];
+    Acc acc[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int nl = warp * 32 * S + s * 32 + lane;
+      const long long n = static_cast<long long>(b) * SB + nl;
+      const float4 x = xs[n];
+      // z = R x + t in FP32 (centred frame)
+      const float z0 = fmaf(Rm[0], x.x, fmaf(Rm[1], x.y, fmaf(Rm[2], x.z, tv[0])));
+      const float z1 = fmaf(Rm[3], x.x, fmaf(Rm[4], x.y, fmaf(Rm[5], x.z, tv[1])));
+      const float z2 = fmaf(Rm[6], x.x, fmaf(Rm[7], x.y, fmaf(Rm[8], x.z, tv[2])));
+      src[s].z0 = dup(z0);
+      src[s].z1 = dup(z1);
+      src[s].z2 = dup(z2);
+      src[s].kp = dup(kap_n ? kap_n[n] : kap_uniform);
+      const float2 zero = make_float2(0.f, 0.f);
+      acc[s] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
+    }
+
+    for (; u < seg_end; ++u, ++i) {
+      const int stage = i % kStages;
+      const uint32_t parity = static_cast<uint32_t>(i / kStages) & 1u;
+      const bool ok = mbar_wait(&full[stage], parity);
+      if (!ok && lane == 0) atomicOr(status, kStatusTimeout);
+      tile_compute<S>(tiles + stage * kTileFloats, src, acc, nc);
+      if (__syncthreads_or(!ok)) {
+        abort = true;
+        break;
+      }
+      if (tid == 0 && i + kStages < n_units) {
+        const long long tile = (u0 + i + kStages) % num_tiles;
+        bulk_load(tiles + stage * kTileFloats, rec + tile * kTileFloats, kTileBytes, &full[stage]);
+      }
+    }
+    if (abort) break;
+    float* dst = part + (static_cast<size_t>(blockIdx.x) * segs_max + seg) * kMom * SB;
+#pragma unroll
+    for (int s = 0; s < S; ++s) store_acc(dst, SB, warp * 32 * S + s * 32 + lane, acc[s]);
+    ++seg;
+  }
+  if (abort && tid == 0) {
+    // let copies still in flight land before the CTA's shared memory is released
+    for (int k = 0; k < kStages; ++k) {
+      const int j = i + 1 + k;
+      if (j < n_units) mbar_wait(&full[j % kStages], static_cast<uint32_t>(j / kStages) & 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-source shift for the max-shift mode (used when w = 0 or the fixed shift
+// could overflow FP32): L_n = max(log2 gamma, max_m (l_m - c d_mn)).
+// ---------------------------------------------------------------------------
+constexpr int kShiftThreads = 128;
+
+__global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __restrict__ xs,
+                                                              const float* __restrict__ rec,
+                                                              const EmState* __restrict__ st,
+                                                              long long N, int num_tiles,
+                                                              float* __restrict__ kap_n,
+                                                              float* __restrict__ gam_n) {
+  __shared__ __align__(16) float tile[7 * kTile];
+  if (st->done) return;
+  const long long n = static_cast<long long>(blockIdx.x) * kShiftThreads + threadIdx.x;
+  const bool valid = n < N;
+  const float4 x = valid ? xs[n] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* R = st->Rf;
+  const float z0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, st->tf[0])));
+  const float z1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, st->tf[1])));
+  const float z2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, st->tf[2])));
+  const float nc = st->neg_c;
+  float best = -INFINITY;
+  const int plane_of[7] = {0, 1, 2, 3, 4, 5, 12};
+  for (int t = 0; t < num_tiles; ++t) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) {
+      const int p = e / kTile, j = e % kTile;
+      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + plane_of[p] * kTile + j];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < kTile; ++j) {
+      const float r0 = z0 + tile[0 * kTile + j];
+      const float r1 = z1 + tile[1 * kTile + j];
+      const float r2 = z2 + tile[2 * kTile + j];
+      const float v = fmaf(tile[3 * kTile + j], r0,
+                           fmaf(tile[4 * kTile + j], r1, tile[5 * kTile + j] * r2));
+      const float d = fmaf(v, v, fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
+      best = fmaxf(best, fmaf(d, nc, tile[6 * kTile + j]));
+    }
+  }
+  if (!valid) return;
+  const float Lg = st->L;  // log2 gamma (-inf without outlier term)
+  const float L = fmaxf(best, Lg);
+  // kappa = L / c with c = -neg_c; gamma' = 2^(log2 gamma - L)
+  kap_n[n] = -L / nc;
+  gam_n[n] = exp2f(Lg - L);
+}
+
+// ---------------------------------------------------------------------------
+// Combine: per source, add the FP32 pieces in FP64 (fixed order), normalise
+// by S0 + gamma'_n, and reduce the FP64 global moments of the M step.
+// ---------------------------------------------------------------------------
+constexpr int kCombineThreads = 256;
+
+// Slot range of source block b inside CTA cta (mirrors the hot kernel's segmentation).
+__device__ __forceinline__ void block_slots(long long units, long long G, int num_tiles, int seg_cap,
+                                            int cta, int b, int& first, int& count) {
+  const long long s0 = static_cast<long long>(cta) * units / G;
+  const long long s1 = static_cast<long long>(cta + 1) * units / G;
+  const long long bs = static_cast<long long>(b) * num_tiles;
+  const long long be = bs + num_tiles;
+  const long long lo = s0 > bs ? s0 : bs;
+  const long long hi = s1 < be ? s1 : be;
+  if (hi <= lo) {
+    first = 0;
+    count = 0;
+    return;
+  }
+  count = static_cast<int>((hi - lo + seg_cap - 1) / seg_cap);
+  const long long bfirst = s0 / num_tiles;
+  if (b == bfirst) {
+    first = 0;
+  } else {
+    const long long len_first = (bfirst + 1) * num_tiles - s0;
+    const long long per_full = (num_tiles + seg_cap - 1) / seg_cap;
+    first = static_cast<int>((len_first + seg_cap - 1) / seg_cap + (b - bfirst - 1) * per_full);
+  }
+}
+
+__device__ __forceinline__ long long owner_cta(long long u, long long units, long long G) {
+  return ((u + 1) * G - 1) / units;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(kCombineThreads)
+    combine_kernel(const float4* __restrict__ xs, long long N, const float* __restrict__ part,
+                   const EmState* __restrict__ st, const float* __restrict__ kap_n,
+                   const float* __restrict__ gam_n, double* __restrict__ blk,
+                   float* __restrict__ per_n, int SB, int num_tiles, long long units, int G,
+                   int seg_cap, int segs_max) {
+  __shared__ double red[kCombineThreads / 32][kGlob];
+  if (st->done) return;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const long long n = static_cast<long long>(blockIdx.x) * kCombineThreads + tid;
+  const bool valid = n < N;
+
+  double m[kMom];
+#pragma unroll
+  for (int k = 0; k < kMom; ++k) m[k] = 0.0;
+  double xt0 = 0, xt1 = 0, xt2 = 0;
+  double kap = 0, gp = 0, L = 0;
+  if (valid) {
+    const int b = static_cast<int>(n / SB);
+    const int nl = static_cast<int>(n % SB);
+    const long long c0 = owner_cta(static_cast<long long>(b) * num_tiles, units, G);
+    const long long c1 = owner_cta(static_cast<long long>(b + 1) * num_tiles - 1, units, G);
+    for (long long c = c0; c <= c1; ++c) {
+      int first, count;
+      block_slots(units, G, num_tiles, seg_cap, static_cast<int>(c), b, first, count);
+      for (int j = first; j < first + count; ++j) {
+        const float* src = part + (static_cast<size_t>(c) * segs_max + j) * kMom * SB + nl;
+#pragma unroll
+        for (int k = 0; k < kMom; ++k) m[k] += static_cast<double>(src[static_cast<size_t>(k) * SB]);
+      }
+    }
+    const float4 x = xs[n];
+    xt0 = x.x;
+    xt1 = x.y;
+    xt2 = x.z;
+    const double nc = st->neg_c;
+    if (kap_n) {
+      kap = kap_n[n];
+      gp = gam_n[n];
+      L = -kap * nc;
+    } else {
+      kap = st->kap;
+      gp = (st->log2_wodds > -INFINITY) ? 1.0 : 0.0;
+      L = st->L;
+    }
+  }
+  // normalisation
+  const double S0 = m[0];
+  const double D = m[13] - kap * S0;
+  const double denom = S0 + gp;
+  const double inv = denom > 0.0 ? 1.0 / denom : 0.0;
+  const double Pb = S0 * inv;
+  const double rho0 = m[1] * inv, rho1 = m[2] * inv, rho2 = m[3] * inv;
+  const double W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv,
+               W12 = m[8] * inv, W22 = m[9] * inv;
+  const double be0 = m[10] * inv, be1 = m[11] * inv, be2 = m[12] * inv;
+  const double Dn = D * inv;
+  const double Pout = gp * inv;
+  const double nll = valid && denom > 0.0 ? st->nll_const - (L * 0.69314718055994530942 + log(denom)) : 0.0;
+  if (valid && per_n) {
+    float* o = per_n + n * 16;
+    const double v[16] = {Pb, rho0, rho1, rho2, W00, W01, W02, W11, W12, W22, be0, be1, be2, Dn, Pout, 0.0};
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = static_cast<float>(v[k]);
+  }
+  const double h[3] = {rho0 + be0, rho1 + be1, rho2 + be2};
+  const double A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
+  const double xt[4] = {xt0, xt1, xt2, valid ? 1.0 : 0.0};
+
+  // contributions, reduced warp by warp into shared memory
+  auto put = [&](int j, double v) {
+    v = warp_sum(v);
+    if (lane == 0) red[warp][j] = v;
+  };
+  put(0, Pb);
+  put(1, Dn);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put(2 + 4 * i + k, h[i] * xt[k]);
+  {
+    int j = 14;
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = k; l < 4; ++l) put(j++, A[p] * xt[k] * xt[l]);
+  }
+  put(74, Pout);
+  put(75, nll);
+  __syncthreads();
+  if (tid < kGlob) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kCombineThreads / 32; ++w) s += red[w][tid];
+    blk[static_cast<size_t>(blockIdx.x) * kGlob + tid] = s;
+  }
+}
+
+template <int S>
+cudaError_t launch_estep_t(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
+                           const float* kap_n, float* part, int* status, cudaStream_t s) {
+  estep_kernel<S><<<p.grid, kNW * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, status,
+                                                        p.num_tiles, p.units, p.seg_cap, p.segs_max);
+  return cudaGetLastError();
+}
+
+int resident_ctas(int S) {
+  int occ = 1;
+  const size_t smem = kStages * kTileBytes + kStages * sizeof(uint64_t);
+  cudaError_t e = cudaSuccess;
+  if (S == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4>, kNW * 32, smem);
+  else if (S == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2>, kNW * 32, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1>, kNW * 32, smem);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return occ;
+}
+
+}  // namespace
+
+EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
+  EstepPlan p{};
+  p.NW = kNW;
+  p.num_tiles = static_cast<int>((M + kTile - 1) / kTile);
+  p.smem_bytes = kStages * kTileBytes + kStages * sizeof(uint64_t);
+  const int cands[3] = {4, 2, 1};
+  int chosen = 1;
+  if (S_override == 1 || S_override == 2 || S_override == 4) {
+    chosen = S_override;
+  } else {
+    for (int c : cands) {
+      const int SB = kNW * 32 * c;
+      const long long blocks = (N + SB - 1) / SB;
+      const long long units = blocks * p.num_tiles;
+      if (units >= 4LL * num_sms * resident_ctas(c)) {
+        chosen = c;
+        break;
+      }
+    }
+  }
+  p.S = chosen;
+  p.SB = kNW * 32 * chosen;
+  p.num_blocks = static_cast<int>((N + p.SB - 1) / p.SB);
+  p.units = static_cast<long long>(p.num_blocks) * p.num_tiles;
+  const long long slots = static_cast<long long>(num_sms) * resident_ctas(chosen);
+  p.grid = static_cast<int>(p.units < slots ? p.units : slots);
+  p.seg_cap = 64;
+  const long long per_cta = (p.units + p.grid - 1) / p.grid;
+  p.segs_max = static_cast<int>((per_cta + p.seg_cap - 1) / p.seg_cap + (per_cta + p.num_tiles - 1) / p.num_tiles + 2);
+  return p;
+}
+
+size_t estep_partial_floats(const EstepPlan& p) {
+  return static_cast<size_t>(p.grid) * p.segs_max * kMom * p.SB;
+}
+
+cudaError_t launch_estep(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
+                         const float* kap_n, float* part, int* /*part_meta*/, int* status,
+                         cudaStream_t s) {
+  switch (p.S) {
+    case 4: return launch_estep_t<4>(p, xs, rec, st, kap_n, part, status, s);
+    case 2: return launch_estep_t<2>(p, xs, rec, st, kap_n, part, status, s);
+    default: return launch_estep_t<1>(p, xs, rec, st, kap_n, part, status, s);
+  }
+}
+
+cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
+                         int64_t N, float* kap_n, float* gam_n, cudaStream_t s) {
+  const long long blocks = (N + kShiftThreads - 1) / kShiftThreads;
+  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, st, N, p.num_tiles,
+                                                                      kap_n, gam_n);
+  return cudaGetLastError();
+}
+
+int combine_blocks(int64_t N) { return static_cast<int>((N + kCombineThreads - 1) / kCombineThreads); }
+
+cudaError_t launch_combine(const EstepPlan& p, const float4* xs, int64_t N, const float* part,
+                           const int* /*part_meta*/, const EmState* st, const float* kap_n,
+                           const float* gam_n, double* blk, float* per_n, cudaStream_t s) {
+  combine_kernel<<<combine_blocks(N), kCombineThreads, 0, s>>>(xs, N, part, st, kap_n, gam_n, blk,
+                                                               per_n, p.SB, p.num_tiles, p.units,
+                                                               p.grid, p.seg_cap, p.segs_max);
+  return cudaGetLastError();
+}
+
+}  // namespace lsg

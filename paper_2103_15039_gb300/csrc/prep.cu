@@ -1,0 +1,512 @@
+// Preprocessing and initialisation kernels of LSG-CPD on sm_103a.
+//
+//  * statistics + centring: FP64 centroids of both clouds, the target's axis-
+//    aligned box (V of the outlier density p_o = 1/V, sides clamped below at
+//    1e-2 of the diagonal), the CPD start value of sigma^2
+//    sum_mn |g0 x_n - y_m|^2 / (3 N M) in closed form, and FP32 centred copies;
+//  * k nearest neighbours of every target (self included): exact brute force
+//    over shared-memory candidate tiles, FP32 squared distances
+//    fma(dz, dz, fma(dy, dy, dx * dx)), ties to the lower index, the candidate
+//    range split over several CTAs and the sorted partial lists merged;
+//  * local surface geometry (Sec. 3.1, Eqs. (2)-(3)): FP64 covariance of the
+//    neighbourhood about its mean, cyclic Jacobi for the smallest eigenpair,
+//    surface variation kappa = lambda_min / trace, penalty
+//    alpha = alpha_max tanh(lambda (1/kappa - 3) / 2), packed into the
+//    E step's tile-major target records.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace lsg {
+namespace {
+
+constexpr int kStatThreads = 256;
+constexpr int kStatBlocksMax = 1024;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block reduction of NV values with per-value operation op (0 sum, 1 min, 2 max).
+template <int NV>
+__device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* out_row) {
+  __shared__ double sh[kStatThreads / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = v[j];
+    x = op[j] == 0 ? warp_sum_d(x) : (op[j] == 1 ? warp_min_d(x) : warp_max_d(x));
+    if (lane == 0) sh[warp][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int j = threadIdx.x;
+    double x = sh[0][j];
+    for (int w = 1; w < kStatThreads / 32; ++w)
+      x = op[j] == 0 ? x + sh[w][j] : (op[j] == 1 ? fmin(x, sh[w][j]) : fmax(x, sh[w][j]));
+    out_row[j] = x;
+  }
+}
+
+// Pass 1: sum x (3), sum y (3), min y (3), max y (3).
+__global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __restrict__ X, long long N,
+                                                                 const float* __restrict__ Y, long long M,
+                                                                 double* __restrict__ red) {
+  double v[12];
+  const int op[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2};
+  for (int j = 0; j < 6; ++j) v[j] = 0.0;
+  for (int j = 6; j < 9; ++j) v[j] = INFINITY;
+  for (int j = 9; j < 12; ++j) v[j] = -INFINITY;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+    v[0] += X[3 * i];
+    v[1] += X[3 * i + 1];
+    v[2] += X[3 * i + 2];
+  }
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < M; i += stride) {
+    const double a = Y[3 * i], b = Y[3 * i + 1], c = Y[3 * i + 2];
+    v[3] += a;
+    v[4] += b;
+    v[5] += c;
+    v[6] = fmin(v[6], a);
+    v[7] = fmin(v[7], b);
+    v[8] = fmin(v[8], c);
+    v[9] = fmax(v[9], a);
+    v[10] = fmax(v[10], b);
+    v[11] = fmax(v[11], c);
+  }
+  block_reduce<12>(v, op, red + static_cast<size_t>(blockIdx.x) * 12);
+}
+
+// Finalise pass 1: centroids, V, diagonal and sigma^2 floor.
+__global__ void finalize_raw_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
+                                    double volume, double floor_rel, EmState* __restrict__ st) {
+  if (threadIdx.x != 0) return;
+  double v[12];
+  for (int j = 0; j < 6; ++j) v[j] = 0.0;
+  for (int j = 6; j < 9; ++j) v[j] = INFINITY;
+  for (int j = 9; j < 12; ++j) v[j] = -INFINITY;
+  for (int b = 0; b < nblk; ++b) {
+    const double* r = red + static_cast<size_t>(b) * 12;
+    for (int j = 0; j < 6; ++j) v[j] += r[j];
+    for (int j = 6; j < 9; ++j) v[j] = fmin(v[j], r[j]);
+    for (int j = 9; j < 12; ++j) v[j] = fmax(v[j], r[j]);
+  }
+  for (int c = 0; c < 3; ++c) {
+    st->mu_x[c] = v[c] / static_cast<double>(N);
+    st->mu_y[c] = v[3 + c] / static_cast<double>(M);
+  }
+  double s[3], d2 = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    s[c] = v[9 + c] - v[6 + c];
+    d2 += s[c] * s[c];
+  }
+  const double diag = sqrt(d2);
+  double V = 1.0;
+  for (int c = 0; c < 3; ++c) V *= fmax(s[c], 1e-2 * diag);
+  st->diag = diag;
+  st->V = volume > 0.0 ? volume : V;
+  st->sigma2_floor = floor_rel * diag * diag;
+}
+
+// Pass 2: centred FP32 copies (sources as float4, padded with zeros up to n_pad)
+// and sums of the centred clouds: sum xc (3), sum |xc|^2, sum yc (3), sum |yc|^2.
+__global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __restrict__ X, long long N,
+                                                              const float* __restrict__ Y, long long M,
+                                                              const EmState* __restrict__ st,
+                                                              float4* __restrict__ xs, long long n_pad,
+                                                              double* __restrict__ red) {
+  double v[8];
+  const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < 8; ++j) v[j] = 0.0;
+  const double mx0 = st->mu_x[0], mx1 = st->mu_x[1], mx2 = st->mu_x[2];
+  const double my0 = st->mu_y[0], my1 = st->mu_y[1], my2 = st->mu_y[2];
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
+    if (i < N) {
+      const double a = X[3 * i] - mx0, b = X[3 * i + 1] - mx1, c = X[3 * i + 2] - mx2;
+      const float fa = static_cast<float>(a), fb = static_cast<float>(b), fc = static_cast<float>(c);
+      xs[i] = make_float4(fa, fb, fc, 0.f);
+      v[0] += fa;
+      v[1] += fb;
+      v[2] += fc;
+      v[3] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
+    } else {
+      xs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < M; i += stride) {
+    const float fa = static_cast<float>(Y[3 * i] - my0);
+    const float fb = static_cast<float>(Y[3 * i + 1] - my1);
+    const float fc = static_cast<float>(Y[3 * i + 2] - my2);
+    v[4] += fa;
+    v[5] += fb;
+    v[6] += fc;
+    v[7] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
+  }
+  block_reduce<8>(v, op, red + static_cast<size_t>(blockIdx.x) * 8);
+}
+
+// Finalise pass 2: initial pose in the centred frame, sigma^2_0, E-step constants.
+// t_c = R0 mu_x + t0 - mu_y;  with z = R0 xc + t_c:
+//   sum z = R0 sum xc + N t_c,  sum |z|^2 = sum |xc|^2 + 2 t_c . (R0 sum xc) + N |t_c|^2,
+//   sigma^2_0 = (M sum|z|^2 + N sum|yc|^2 - 2 sum z . sum yc) / (3 N M).
+__global__ void finalize_init_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
+                                     DevParams dp, EmState* __restrict__ st) {
+  if (threadIdx.x != 0) return;
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < nblk; ++b)
+    for (int j = 0; j < 8; ++j) v[j] += red[static_cast<size_t>(b) * 8 + j];
+  const double* R = dp.init_R;
+  double tc[3], Rsx[3];
+  for (int i = 0; i < 3; ++i) {
+    tc[i] = R[3 * i] * st->mu_x[0] + R[3 * i + 1] * st->mu_x[1] + R[3 * i + 2] * st->mu_x[2] +
+            dp.init_t[i] - st->mu_y[i];
+    Rsx[i] = R[3 * i] * v[0] + R[3 * i + 1] * v[1] + R[3 * i + 2] * v[2];
+  }
+  const double Nd = static_cast<double>(N), Md = static_cast<double>(M);
+  double sz[3], zz = v[3] + Nd * (tc[0] * tc[0] + tc[1] * tc[1] + tc[2] * tc[2]);
+  for (int i = 0; i < 3; ++i) {
+    sz[i] = Rsx[i] + Nd * tc[i];
+    zz += 2.0 * tc[i] * Rsx[i];
+  }
+  const double cross = sz[0] * v[4] + sz[1] * v[5] + sz[2] * v[6];
+  const double s20 = (Md * zz + Nd * v[7] - 2.0 * cross) / (3.0 * Nd * Md);
+  for (int i = 0; i < 9; ++i) st->R[i] = R[i];
+  for (int i = 0; i < 3; ++i) st->t[i] = tc[i];
+  double s2 = dp.sigma2_init > 0.0 ? dp.sigma2_init : s20;
+  if (!(s2 > st->sigma2_floor)) s2 = st->sigma2_floor > 0.0 ? st->sigma2_floor : 1e-30;
+  st->sigma2 = s2;
+  st->log2_wodds = dp.w > 0.0 ? log2(dp.w) - log2(1.0 - dp.w) : -INFINITY;
+  st->done = 0;
+  st->iter = 0;
+  st->numeric_fail = 0;
+  // E-step constants (same definitions as the M-step kernel)
+  const double c = 1.4426950408889634 / (2.0 * s2);
+  const double L = st->log2_wodds + 1.5 * log2(2.0 * 3.14159265358979323846 * s2) - log2(st->V);
+  for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
+  for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
+  st->neg_c = static_cast<float>(-c);
+  st->L = static_cast<float>(L);
+  st->kap = static_cast<float>(L / c);
+  st->nll_const = -log1p(-dp.w) + 1.5 * log(2.0 * 3.14159265358979323846 * s2);
+}
+
+// ---------------------------------------------------------------------------
+// kNN
+// ---------------------------------------------------------------------------
+constexpr int kKnnThreads = 128;
+constexpr int kKnnTile = 512;
+
+__global__ void to_float4_kernel(const float* __restrict__ Y, long long M, float4* __restrict__ y4) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < M) y4[i] = make_float4(Y[3 * i], Y[3 * i + 1], Y[3 * i + 2], 0.f);
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* __restrict__ y4, long long M,
+                                                                  int k, int splits,
+                                                                  float* __restrict__ part_d,
+                                                                  int* __restrict__ part_i) {
+  __shared__ float4 cand[kKnnTile];
+  const long long q = static_cast<long long>(blockIdx.x) * kKnnThreads + threadIdx.x;
+  const int split = blockIdx.y;
+  const long long per = (M + splits - 1) / splits;
+  const long long c_lo = split * per;
+  long long c_hi = c_lo + per;
+  if (c_hi > M) c_hi = M;
+  const bool valid = q < M;
+  const float4 p = valid ? y4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float bd[KMAX];
+  int bi[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    bd[j] = INFINITY;
+    bi[j] = 0x7fffffff;
+  }
+  float thr = INFINITY;  // current k-th best
+  for (long long base = c_lo; base < c_hi; base += kKnnTile) {
+    const int cnt = static_cast<int>((c_hi - base) < kKnnTile ? (c_hi - base) : kKnnTile);
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt; j += kKnnThreads) cand[j] = y4[base + j];
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+      const float4 c = cand[j];
+      const float dx = __fsub_rn(p.x, c.x);
+      const float dy = __fsub_rn(p.y, c.y);
+      const float dz = __fsub_rn(p.z, c.z);
+      const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+      if (d < thr) {
+        const int ci = static_cast<int>(base + j);
+        // insert (d, ci) into the sorted list of the first k entries; an equal
+        // distance already present (lower index) stays first
+#pragma unroll
+        for (int s = KMAX - 1; s >= 0; --s) {
+          if (s < k) {
+            if (s > 0 && bd[s - 1] > d) {
+              bd[s] = bd[s - 1];
+              bi[s] = bi[s - 1];
+            } else if (bd[s] > d) {
+              bd[s] = d;
+              bi[s] = ci;
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < KMAX; ++s)
+          if (s == k - 1) thr = bd[s];
+      }
+    }
+  }
+  if (!valid) return;
+  float* od = part_d + (static_cast<size_t>(split) * M + q) * k;
+  int* oi = part_i + (static_cast<size_t>(split) * M + q) * k;
+#pragma unroll
+  for (int s = 0; s < KMAX; ++s)
+    if (s < k) {
+      od[s] = bd[s];
+      oi[s] = bi[s];
+    }
+}
+
+// Merge the sorted partial lists of every split by (distance, index).
+__global__ void knn_merge_kernel(const float* __restrict__ part_d, const int* __restrict__ part_i,
+                                 long long M, int k, int splits, int* __restrict__ idx) {
+  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= M) return;
+  int head[64];
+  for (int s = 0; s < splits; ++s) head[s] = 0;
+  for (int r = 0; r < k; ++r) {
+    int best = -1;
+    float bd = INFINITY;
+    int bi = 0x7fffffff;
+    for (int s = 0; s < splits; ++s) {
+      if (head[s] >= k) continue;
+      const size_t o = (static_cast<size_t>(s) * M + q) * k + head[s];
+      const float d = part_d[o];
+      const int i = part_i[o];
+      if (d < bd || (d == bd && i < bi)) {
+        bd = d;
+        bi = i;
+        best = s;
+      }
+    }
+    if (best < 0) break;
+    ++head[best];
+    idx[q * k + r] = bi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Local geometry + record packing
+// ---------------------------------------------------------------------------
+
+// Cyclic Jacobi for a symmetric 3x3 matrix (FP64); returns the eigenvalues and
+// the eigenvectors (columns of V).
+__device__ void jacobi_sym3(double A[3][3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double dg = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off == 0.0 || off <= 1e-34 * dg) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const double apq = A[p][q];
+      if (apq == 0.0) continue;
+      const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+      const double t = copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+      const double c = rsqrt(t * t + 1.0);
+      const double s = t * c;
+      // A' = J^T A J with J = [[c, s], [-s, c]] acting on (p, q)
+      const double app = A[p][p] - t * apq;
+      const double aqq = A[q][q] + t * apq;
+      const int r = 3 - p - q;
+      const double arp = A[r][p], arq = A[r][q];
+      A[r][p] = A[p][r] = c * arp - s * arq;
+      A[r][q] = A[q][r] = s * arp + c * arq;
+      A[p][p] = app;
+      A[q][q] = aqq;
+      A[p][q] = A[q][p] = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        const double vip = V[i][p], viq = V[i][q];
+        V[i][p] = c * vip - s * viq;
+        V[i][q] = s * vip + c * viq;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void write_record(float* rec, long long m, float ny0, float ny1, float ny2,
+                                             float a0, float a1, float a2, float l) {
+  const long long tile = m / kTile;
+  const int j = static_cast<int>(m % kTile);
+  float* r = rec + tile * kTileFloats + j;
+  const float v[kPlanes] = {ny0, ny1, ny2, a0, a1, a2, a0 * a0, a0 * a1, a0 * a2, a1 * a1, a1 * a2, a2 * a2, l};
+#pragma unroll
+  for (int p = 0; p < kPlanes; ++p) r[p * kTile] = v[p];
+}
+
+__device__ __forceinline__ void pack_target(float* rec, long long m, const float* Y, const EmState* st,
+                                            double nx, double ny, double nz, double alpha, double log2_pi,
+                                            int alpha_norm) {
+  const double sa = sqrt(alpha > 0.0 ? alpha : 0.0);
+  const double l = log2_pi + (alpha_norm ? 0.5 * log2(1.0 + alpha) : 0.0);
+  write_record(rec, m, static_cast<float>(-(Y[3 * m] - st->mu_y[0])),
+               static_cast<float>(-(Y[3 * m + 1] - st->mu_y[1])),
+               static_cast<float>(-(Y[3 * m + 2] - st->mu_y[2])), static_cast<float>(sa * nx),
+               static_cast<float>(sa * ny), static_cast<float>(sa * nz), static_cast<float>(l));
+}
+
+__global__ void geometry_kernel(const float* __restrict__ Y, long long M, const int* __restrict__ idx, int k,
+                                double alpha_max, double lambda, int alpha_norm,
+                                const EmState* __restrict__ st, float* __restrict__ rec, long long m_pad,
+                                float* __restrict__ normals, float* __restrict__ kappa,
+                                float* __restrict__ alpha_out) {
+  const long long m = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= m_pad) return;
+  if (m >= M) {
+    write_record(rec, m, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    return;
+  }
+  double mean[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < k; ++j) {
+    const long long q = idx[m * k + j];
+    mean[0] += Y[3 * q];
+    mean[1] += Y[3 * q + 1];
+    mean[2] += Y[3 * q + 2];
+  }
+  for (int c = 0; c < 3; ++c) mean[c] /= k;
+  double C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int j = 0; j < k; ++j) {
+    const long long q = idx[m * k + j];
+    const double d[3] = {Y[3 * q] - mean[0], Y[3 * q + 1] - mean[1], Y[3 * q + 2] - mean[2]};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) C[r][c] += d[r] * d[c] / k;
+  }
+  double V[3][3];
+  jacobi_sym3(C, V);
+  int i0 = 0;
+  if (C[1][1] < C[i0][i0]) i0 = 1;
+  if (C[2][2] < C[i0][i0]) i0 = 2;
+  const double l0 = fmax(C[i0][i0], 0.0);
+  const double tr = fmax(C[0][0], 0.0) + fmax(C[1][1], 0.0) + fmax(C[2][2], 0.0);
+  double kap, n0, n1, n2;
+  if (tr > 0.0) {
+    kap = l0 / tr;
+    n0 = V[0][i0];
+    n1 = V[1][i0];
+    n2 = V[2][i0];
+  } else {
+    kap = 1.0 / 3.0;
+    n0 = 0.0;
+    n1 = 0.0;
+    n2 = 1.0;
+  }
+  double a = kap > 0.0 ? alpha_max * tanh(0.5 * lambda * (1.0 / kap - 3.0)) : alpha_max;
+  if (a < 0.0) a = 0.0;
+  pack_target(rec, m, Y, st, n0, n1, n2, a, -log2(static_cast<double>(M)), alpha_norm);
+  if (normals) {
+    normals[3 * m] = static_cast<float>(n0);
+    normals[3 * m + 1] = static_cast<float>(n1);
+    normals[3 * m + 2] = static_cast<float>(n2);
+  }
+  if (kappa) kappa[m] = static_cast<float>(kap);
+  if (alpha_out) alpha_out[m] = static_cast<float>(a);
+}
+
+__global__ void pack_kernel(const float* __restrict__ Y, const float* __restrict__ normals,
+                            const float* __restrict__ alpha, long long M, int alpha_norm,
+                            const EmState* __restrict__ st, float* __restrict__ rec, long long m_pad) {
+  const long long m = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (m >= m_pad) return;
+  if (m >= M) {
+    write_record(rec, m, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    return;
+  }
+  pack_target(rec, m, Y, st, normals[3 * m], normals[3 * m + 1], normals[3 * m + 2], alpha[m],
+              -log2(static_cast<double>(M)), alpha_norm);
+}
+
+}  // namespace
+
+int stats_blocks(int64_t n) {
+  const long long b = (n + kStatThreads - 1) / kStatThreads;
+  return static_cast<int>(b < kStatBlocksMax ? (b > 0 ? b : 1) : kStatBlocksMax);
+}
+
+cudaError_t launch_center_only(const float* X, int64_t N, const float* Y, int64_t M, double* red,
+                               EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
+  const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : M);
+  raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
+  finalize_raw_kernel<<<1, 32, 0, s>>>(red, nb, N, M, 0.0, 0.0, st);
+  center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red + static_cast<size_t>(kStatBlocksMax) * 12);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const float* X, int64_t N, const float* Y, int64_t M, const DevParams& dp,
+                        double* red, EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
+  const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : (n_pad > M ? n_pad : M));
+  raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
+  finalize_raw_kernel<<<1, 32, 0, s>>>(red, nb, N, M, dp.volume, dp.sigma2_floor_rel, st);
+  double* red2 = red + static_cast<size_t>(kStatBlocksMax) * 12;
+  center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red2);
+  finalize_init_kernel<<<1, 32, 0, s>>>(red2, nb, N, M, dp, st);
+  return cudaGetLastError();
+}
+
+int knn_splits(int64_t M, int num_sms) {
+  const long long qblocks = (M + kKnnThreads - 1) / kKnnThreads;
+  long long sp = (4LL * num_sms + qblocks - 1) / qblocks;
+  if (sp < 1) sp = 1;
+  if (sp > 32) sp = 32;
+  // at least 64 candidates per split
+  while (sp > 1 && M / sp < 64) --sp;
+  return static_cast<int>(sp);
+}
+
+cudaError_t launch_knn(const float* Y, int64_t M, int k, float4* y4, float* part_d, int* part_i,
+                       int* idx_out, int splits, cudaStream_t s) {
+  to_float4_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, s>>>(Y, M, y4);
+  dim3 grid(static_cast<unsigned>((M + kKnnThreads - 1) / kKnnThreads), static_cast<unsigned>(splits));
+  if (k <= 16)
+    knn_partial_kernel<16><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
+  else
+    knn_partial_kernel<32><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
+  knn_merge_kernel<<<static_cast<unsigned>((M + 127) / 128), 128, 0, s>>>(part_d, part_i, M, k, splits,
+                                                                         idx_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_geometry(const float* Y, int64_t M, const int* idx, int k, double alpha_max,
+                            double lambda, int alpha_norm, const EmState* st, float* rec, int num_tiles,
+                            float* normals, float* kappa, float* alpha, cudaStream_t s) {
+  const long long m_pad = static_cast<long long>(num_tiles) * kTile;
+  geometry_kernel<<<static_cast<unsigned>((m_pad + 127) / 128), 128, 0, s>>>(
+      Y, M, idx, k, alpha_max, lambda, alpha_norm, st, rec, m_pad, normals, kappa, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float* Y, const float* normals, const float* alpha, int64_t M, int alpha_norm,
+                        const EmState* st, float* rec, int num_tiles, cudaStream_t s) {
+  const long long m_pad = static_cast<long long>(num_tiles) * kTile;
+  pack_kernel<<<static_cast<unsigned>((m_pad + 127) / 128), 128, 0, s>>>(Y, normals, alpha, M, alpha_norm,
+                                                                         st, rec, m_pad);
+  return cudaGetLastError();
+}
+
+}  // namespace lsg

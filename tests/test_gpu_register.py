@@ -1,0 +1,102 @@
+"""Full registrations on the GPU against the FP64 oracle from the same start.
+
+The bar for FP32 E steps: rotation error < 1e-4 rad and translation error
+< 1e-5 of the target's bounding-box diagonal relative to the oracle's result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_15039_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = binding.Context(0, 25000, 25000)
+    yield c
+    c.close()
+
+
+def _diag(Y):
+    Y = np.asarray(Y, dtype=np.float64)
+    return float(np.linalg.norm(Y.max(0) - Y.min(0)))
+
+
+def _check(got, ref, Y, rot_tol=1e-4, trans_tol=1e-5):
+    rot = oracle.rotation_error(got["R"], ref["R"])
+    tr = np.linalg.norm(got["t"] - ref["t"]) / _diag(Y)
+    assert rot < rot_tol and tr < trans_tol, (rot, tr)
+    return rot, tr
+
+
+def test_register_sphere_plane_1000(ctx):
+    c = synth.sphere_plane_pair()
+    p = binding.default_params()
+    got = ctx.register(c["X"], c["Y"], p, trace=True)
+    ref = oracle.register(c["X"], c["Y"])
+    _check(got, ref, c["Y"])
+    assert got["iters"] == ref["iters"] == 50
+    assert got["sigma2"] == pytest.approx(ref["sigma2"], rel=1e-3)
+    np.testing.assert_allclose(got["trace"][:, 0], ref["trace"][:, 0], rtol=2e-3)
+    np.testing.assert_allclose(got["trace"][:, 6], ref["trace"][:, 6], rtol=1e-4)
+
+
+def test_register_host_and_device_inputs_agree(ctx):
+    import torch
+    c = synth.sphere_plane_pair(seed=9, n=700, m=900)
+    p = binding.default_params(max_iters=20)
+    a = ctx.register(c["X"], c["Y"], p)
+    b = ctx.register(torch.from_numpy(c["X"]).cuda(), torch.from_numpy(c["Y"]).cuda(), p)
+    np.testing.assert_array_equal(a["R"], b["R"])
+    np.testing.assert_array_equal(a["t"], b["t"])
+
+
+def test_register_is_deterministic(ctx):
+    c = synth.sphere_plane_pair(seed=10, n=1500, m=1300)
+    p = binding.default_params(max_iters=15)
+    a = ctx.register(c["X"], c["Y"], p)
+    b = ctx.register(c["X"], c["Y"], p)
+    np.testing.assert_array_equal(a["R"], b["R"])
+    assert a["sigma2"] == b["sigma2"]
+
+
+def test_register_exact_recovery(ctx):
+    c = synth.sphere_plane_pair(seed=41, n=10, m=1000)
+    Y = c["Y"]
+    rng = np.random.default_rng(41)
+    R0 = synth.random_rotation(rng, 0.5)
+    t0 = np.array([0.05, -0.02, 0.03])
+    X = ((Y.astype(np.float64) - t0) @ R0).astype(np.float32)
+    got = ctx.register(X, Y, binding.default_params(w=0.01, max_iters=100))
+    assert oracle.rotation_error(got["R"], R0) < 1e-5
+    assert np.linalg.norm(got["t"] - t0) < 1e-5
+
+
+@pytest.mark.parametrize("w", [0.0, 0.3])
+def test_register_outlier_weights(ctx, w):
+    c = synth.sphere_plane_pair(seed=12, n=800, m=900)
+    got = ctx.register(c["X"], c["Y"], binding.default_params(w=w, max_iters=30))
+    ref = oracle.register(c["X"], c["Y"], w=w, max_iters=30)
+    _check(got, ref, c["Y"])
+    assert got["mode"] == (1 if w == 0.0 else 0)
+
+
+def test_register_batch_shapes(ctx):
+    """Uneven pairs shaped like the batched workload (first 6 pairs, sizes capped)."""
+    pairs = synth.batch_pairs(num_pairs=6, n_hi=6000)
+    for pr in pairs:
+        got = ctx.register(pr["X"], pr["Y"], binding.default_params(max_iters=20))
+        ref = oracle.register(pr["X"], pr["Y"], max_iters=20)
+        _check(got, ref, pr["Y"])
+
+
+def test_register_rgbd_full_size(ctx):
+    """The benchmark's workload (20,000 x 20,000, RGBD room), first 8 iterations."""
+    c = synth.rgbd_room_pair()
+    p = binding.default_params(max_iters=8)
+    got = ctx.register(c["X"], c["Y"], p, trace=True)
+    ref = oracle.register(c["X"], c["Y"], max_iters=8)
+    _check(got, ref, c["Y"])
+    np.testing.assert_allclose(got["trace"][:, 1], ref["trace"][:, 1], rtol=1e-4)
