@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the LSG-CPD E-step / EM engine on GB300.
+
+A step = one full registration of the RGBD-shaped pair (20,000 x 20,000 points,
+synthetic room ray-cast from a 160 x 125 pinhole camera): preprocessing (kNN,
+normals, surface variation, penalties), initialisation and 50 EM iterations
+(fused E step + FP64 moment combine + FP64 Newton M step), through the C ABI.
+
+value = E-step pair evaluations per second (50 x N x M per step) with the
+inputs resident in HBM; e2e = the same metric through the same C call with
+pinned host inputs (H2D inside the call, result read back to the host).
+The roofline object reports the hot E-step kernel, timed live with CUDA events
+on the stream it is launched on, against the FP32-pipe peak (ALU bound).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank registers its own independent pair (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E-step pair-evals/sec & EM iters/sec at 1 GB300; % FP32/SFU roofline; rot err vs FP64"
+UNIT = "pair-evals/s"
+FLOPS_PER_PAIR = 27  # FP32-pipe operations per (source, target) pair, the fixed algorithmic count
+EX2_PER_PAIR = 1
+SM_MAX_MHZ_NOMINAL = 2070.0
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+# bytes lsgcpd_register reads back per call: the 272-byte device EM state twice
+# (after initialisation and at the end) and the 4-byte status word twice
+D2H_BYTES = 2 * 272 + 2 * 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank):
+    from paper_2103_15039_gb300 import synth
+    seed = synth.SEED_BASE + 2 + 1000 * rank
+    c = synth.rgbd_room_pair(seed=seed)
+    return c, seed
+
+
+def config_obj(c, seed, iters, n_gpus):
+    return {"workload": "rgbd_room_20000x20000", "N": int(len(c["X"])), "M": int(len(c["Y"])),
+            "em_iters": iters, "knn_k": 10, "w": 0.1, "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
+            "overlap": round(float(c["overlap"]), 4), "e_step": "fp32 (packed f32x2) + ex2.approx",
+            "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
+            "parallelism": f"replicas x{n_gpus} (independent pairs per GPU)"}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def profile_traffic():
+    """DRAM traffic per E-step launch from the committed ncu summary, if it was taken
+    on the current kernel source (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "estep_rgbd20k_traffic.json")
+    src = os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", "estep.cu")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if prof.get("estep_cu_sha256") != h:
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(c, got, iters, budget_s=40.0):
+    """The FP64 oracle timed on this host's cores on the same pair.
+
+    If the whole registration fits the budget (estimated from one E step on a
+    subset of sources) it is run in full, which also gives the rotation and
+    translation error of the GPU result against FP64; otherwise a bounded
+    subset of one E step is timed."""
+    import numpy as np
+
+    import oracle
+    X, Y = c["X"], c["Y"]
+    N, M = len(X), len(Y)
+    cores = os.cpu_count() or 1
+    pre = oracle.preprocess(Y, 10, 2.0, 0.2)
+    V, diag = oracle.volume(Y)
+    ns = min(N, 2000)
+    t0 = time.perf_counter()
+    oracle.estep(X[:ns], Y, pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), 0.05, 0.1, V)
+    dt = time.perf_counter() - t0
+    rate = ns * M / dt
+    est_full = iters * N * M / rate
+    out = {"unit": UNIT, "cores": cores, "kind": "oracle", "cpu": oracle.cpu_model()}
+    if est_full <= budget_s:
+        t0 = time.perf_counter()
+        ref = oracle.register(X, Y, max_iters=iters)
+        dt = time.perf_counter() - t0
+        out["value"] = ref["iters"] * N * M / dt
+        out["sample"] = f"full registration: kNN + geometry + {ref['iters']} EM iterations of the same pair"
+        out["seconds"] = round(dt, 2)
+        err = {"rot_err_rad": oracle.rotation_error(got["R"], ref["R"]),
+               "trans_err_rel_diag": float(np.linalg.norm(got["t"] - ref["t"]) / diag),
+               "sigma2_rel": abs(got["sigma2"] - ref["sigma2"]) / ref["sigma2"]}
+        return out, err
+    ns = max(1, min(N, int(20.0 * rate / M)))
+    t0 = time.perf_counter()
+    oracle.estep(X[:ns], Y, pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), 0.05, 0.1, V)
+    dt = time.perf_counter() - t0
+    out["value"] = ns * M / dt
+    out["sample"] = f"one E step over {ns} of {N} sources x {M} targets"
+    out["seconds"] = round(dt, 2)
+    return out, None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_15039_gb300 import binding
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    c, seed = workload(rank)
+    N, M = len(c["X"]), len(c["Y"])
+    iters = args.iters
+    ctx = binding.Context(local, N, M)
+    p = binding.default_params(max_iters=iters)
+    Xd = torch.from_numpy(c["X"]).cuda()
+    Yd = torch.from_numpy(c["Y"]).cuda()
+    Xh = torch.from_numpy(c["X"]).pin_memory()
+    Yh = torch.from_numpy(c["Y"]).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx.set_timing(True)
+    for _ in range(max(args.warmup, 0)):
+        got = ctx.register(Xd, Yd, p)
+        ctx.register(Xh, Yh, p)
+
+    # --- device-resident timed region ---
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, estep_ms, launches = [], [], 0
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = ctx.register(Xd, Yd, p)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        tm = ctx.last_timing()
+        estep_ms.append(tm["ms_estep"])
+        launches += tm["launches"]
+    barrier()
+    clk = clocks.stop()
+    iters_run = got["iters"]
+
+    # --- end-to-end: pinned host inputs, copies inside the C call, result on the host ---
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.register(Xh, Yh, p)
+        e2e_s.append(time.perf_counter() - t0)
+    assert np.allclose(r["R"], got["R"]) and np.allclose(r["t"], got["t"])
+
+    ms = statistics.mean(step_ms)
+    e2e_ms = statistics.mean(e2e_s) * 1e3
+    if ws > 1:
+        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(tt[0]), float(tt[1])
+    pairs_per_step = iters_run * N * M
+    value = ws * pairs_per_step / (ms / 1e3)
+    e2e_value = ws * pairs_per_step / (e2e_ms / 1e3)
+
+    # roofline of the hot kernel (E step): per-launch time measured live
+    t_launch = statistics.mean(estep_ms) / iters_run / 1e3
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32-pipe Top/s
+    achieved = FLOPS_PER_PAIR * N * M / t_launch / 1e12
+    ex2_rate = EX2_PER_PAIR * N * M / t_launch
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": profile_traffic(),
+            "kernel": "estep_kernel", "ms_per_launch": round(t_launch * 1e3, 5),
+            "pairs_per_s_per_launch": N * M / t_launch,
+            "counted": f"{FLOPS_PER_PAIR} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, N*M pairs per launch",
+            "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)",
+            "ex2_per_s": ex2_rate}
+    if clk.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = round(achieved / (sms * FP32_LANES_PER_SM * clk["sm_mhz"] * 1e6 / 1e12), 4)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config_obj(c, seed, iters, ws),
+           "em_iters_per_s": ws * iters_run / (ms / 1e3),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (N + M) * 12,
+                   "d2h_bytes_per_step": D2H_BYTES, "ms_per_step": round(e2e_ms, 4), "clock": "host wall"},
+           "roofline": roof, "clocks": clk, "gpu_launches": launches,
+           "mode": got["mode"], "iters_run": iters_run}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, err = cpu_baseline(c, got, iters_run)
+        out["cpu_baseline"] = cb
+        if err:
+            out["vs_fp64_oracle"] = err
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands on this host's cores: each step is one EM
+    iteration (E step over a bounded subset of the sources, all targets), sized so
+    the whole run stays within a few minutes."""
+    import numpy as np
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    c, seed = workload(0)
+    X, Y = c["X"], c["Y"]
+    N, M = len(X), len(Y)
+    pre = oracle.preprocess(Y, 10, 2.0, 0.2)
+    V, _ = oracle.volume(Y)
+    s2 = oracle.sigma2_init(X, Y, np.eye(3), np.zeros(3))
+    # size one step at about 6 s of CPU work
+    ns = min(N, 1000)
+    t0 = time.perf_counter()
+    oracle.estep(X[:ns], Y, pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), s2, 0.1, V)
+    rate = ns * M / (time.perf_counter() - t0)
+    ns = max(1, min(N, int(6.0 * rate / M)))
+    Xs = X[:ns]
+
+    def step():
+        o = oracle.estep(Xs, Y, pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), s2, 0.1, V)
+        oracle.mstep(o["stats"], Xs, np.eye(3), np.zeros(3))
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+    ms = statistics.mean(times) * 1e3
+    value = ns * M / (ms / 1e3)
+    cores = os.cpu_count() or 1
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_obj(c, seed, args.iters, ws),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"one EM iteration (E step + Newton M step) over {ns} of {N} sources "
+                                      f"x {M} targets per step", "cpu": oracle.cpu_model()},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
