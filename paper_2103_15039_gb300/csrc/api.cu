@@ -234,6 +234,16 @@ cudaError_t ensure_iter_events(lsgcpd_ctx* c, int iters) {
   return cudaSuccess;
 }
 
+// Elapsed ms between two recorded events; 0 (and the error cleared) if unavailable.
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return ms;
+}
+
 // Centred-frame moments -> caller's frame (x~_raw = T x~_c, T = [[I, mu_x], [0, 1]]).
 void moments_to_raw(const double* mc, const double mu[3], double* mr) {
   for (int j = 0; j < LSGCPD_MOMENTS; ++j) mr[j] = mc[j];
@@ -458,9 +468,8 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   LSG_CUDA(leave(c, stream), "stream");
   c->launches = launches;
   if (c->timing) {
-    float a = 0, b = 0;
-    cudaEventElapsedTime(&a, c->t_begin, c->t_prep);
-    cudaEventElapsedTime(&b, c->t_prep, c->t_end);
+    const double a = elapsed_ms(c->t_begin, c->t_prep);
+    const double b = elapsed_ms(c->t_prep, c->t_end);
     c->last_timing[0] = a + b;
     c->last_timing[1] = a;
     c->last_timing[2] = b;
@@ -585,19 +594,19 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
       LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
       cudaError_t ce = cudaSuccess;
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
-        if (c->timing) ce = cudaEventRecord(c->t_iter[4 * it], s);
+        if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
         if (ce == cudaSuccess && mode == 1)
           ce = launch_shift(plan, c->xs.p, c->rec.p, c->st, N, c->kap_n.p, c->gam_n.p, s);
         if (ce == cudaSuccess)
           ce = launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p, nullptr,
                             c->status, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecord(c->t_iter[4 * it + 1], s);
+        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
           ce = launch_combine(plan, c->xs.p, N, c->part.p, nullptr, c->st, mode ? c->kap_n.p : nullptr,
                               mode ? c->gam_n.p : nullptr, c->blk.p, nullptr, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecord(c->t_iter[4 * it + 2], s);
+        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
         if (ce == cudaSuccess) ce = launch_mstep(c->blk.p, nblk, c->st, dp, c->trace.p, nullptr, 0, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecord(c->t_iter[4 * it + 3], s);
+        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
       }
       cudaError_t ee = cudaStreamEndCapture(s, &g);
       if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -635,18 +644,13 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
   out->ms_estep = 0;
   out->ms_total = 0;
   if (c->timing) {
-    float tot = 0, prep = 0;
-    cudaEventElapsedTime(&tot, c->t_begin, c->t_end);
-    cudaEventElapsedTime(&prep, c->t_begin, c->t_prep);
+    const double tot = elapsed_ms(c->t_begin, c->t_end);
+    const double prep = elapsed_ms(c->t_begin, c->t_prep);
     double es = 0, cb = 0, ms = 0;
     for (int it = 0; it < iters; ++it) {
-      float a = 0, b = 0, d = 0;
-      cudaEventElapsedTime(&a, c->t_iter[4 * it], c->t_iter[4 * it + 1]);
-      cudaEventElapsedTime(&b, c->t_iter[4 * it + 1], c->t_iter[4 * it + 2]);
-      cudaEventElapsedTime(&d, c->t_iter[4 * it + 2], c->t_iter[4 * it + 3]);
-      es += a;
-      cb += b;
-      ms += d;
+      es += elapsed_ms(c->t_iter[4 * it], c->t_iter[4 * it + 1]);
+      cb += elapsed_ms(c->t_iter[4 * it + 1], c->t_iter[4 * it + 2]);
+      ms += elapsed_ms(c->t_iter[4 * it + 2], c->t_iter[4 * it + 3]);
     }
     c->last_timing[0] = tot;
     c->last_timing[1] = es;

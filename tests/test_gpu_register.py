@@ -100,3 +100,18 @@ def test_register_rgbd_full_size(ctx):
     ref = oracle.register(c["X"], c["Y"], max_iters=8)
     _check(got, ref, c["Y"])
     np.testing.assert_allclose(got["trace"][:, 1], ref["trace"][:, 1], rtol=1e-4)
+
+
+def test_timing_enabled_calls_report_kernel_times_and_leave_no_error(ctx):
+    c = synth.sphere_plane_pair(seed=13, n=900, m=800)
+    p = binding.default_params(max_iters=10)
+    ctx.set_timing(True)
+    try:
+        a = ctx.register(c["X"], c["Y"], p)
+        t = ctx.last_timing()
+        assert 0 < t["ms_estep"] < t["ms_total"]
+        assert t["ms_combine"] > 0 and t["ms_mstep"] > 0 and t["launches"] > 30
+        b = ctx.register(c["X"], c["Y"], p)  # the next call must not see a stale error
+        np.testing.assert_array_equal(a["R"], b["R"])
+    finally:
+        ctx.set_timing(False)
