@@ -39,9 +39,6 @@ EX2_PER_PAIR = 1
 SM_MAX_MHZ_NOMINAL = 2070.0
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
-# bytes lsgcpd_register reads back per call: the 272-byte device EM state twice
-# (after initialisation and at the end) and the 4-byte status word twice
-D2H_BYTES = 2 * 272 + 2 * 4
 
 
 def parse():
@@ -258,6 +255,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         r = ctx.register(Xh, Yh, p)
         e2e_s.append(time.perf_counter() - t0)
+    xfer = ctx.last_timing()
     assert np.allclose(r["R"], got["R"]) and np.allclose(r["t"], got["t"])
 
     ms = statistics.mean(step_ms)
@@ -291,8 +289,9 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": config_obj(c, seed, iters, ws),
            "em_iters_per_s": ws * iters_run / (ms / 1e3),
-           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (N + M) * 12,
-                   "d2h_bytes_per_step": D2H_BYTES, "ms_per_step": round(e2e_ms, 4), "clock": "host wall"},
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
+                   "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4),
+                   "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
            "mode": got["mode"], "iters_run": iters_run}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

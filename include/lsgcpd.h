@@ -115,10 +115,12 @@ const char* lsgcpd_last_error(const lsgcpd_ctx* ctx);
  * lsgcpd_result.ms_* and lsgcpd_last_timing(). */
 lsgcpd_status lsgcpd_set_timing(lsgcpd_ctx* ctx, int enable);
 
-/* Device times (ms) of the last call: [0] total, [1] E-step kernels, [2]
- * combine kernels, [3] M-step kernels, [4] preprocessing; [5] number of
- * E-step launches timed.  Returns EINVAL if timing is off. */
-lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* ctx, double out[6]);
+/* Figures of the last call.  Device times in ms (timing enabled only):
+ * [0] total, [1] E-step kernels, [2] combine + reduction kernels, [3] M-step
+ * kernels, [4] preprocessing and initialisation.  Always: [5] kernel launches,
+ * [6] bytes copied host -> device, [7] bytes copied device -> host.
+ * Returns EINVAL (after filling out) if timing is off. */
+lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* ctx, double out[8]);
 
 /* Local surface geometry of the target (Sec. 3.1, Eqs. (2)-(3)): for every
  * target m, its k nearest targets (self included, ties to the lower index,

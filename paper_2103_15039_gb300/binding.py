@@ -236,10 +236,10 @@ def lsgcpd_set_timing(ctx, enable):
 
 
 def lsgcpd_last_timing(ctx):
-    out = np.zeros(6)
+    out = np.zeros(8)
     lib().lsgcpd_last_timing(ctx, out.ctypes.data_as(C.POINTER(C.c_double)))
     return dict(ms_total=out[0], ms_estep=out[1], ms_combine=out[2], ms_mstep=out[3], ms_prep=out[4],
-                launches=int(out[5]))
+                launches=int(out[5]), h2d_bytes=int(out[6]), d2h_bytes=int(out[7]))
 
 
 class Context:

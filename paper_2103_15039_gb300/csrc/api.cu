@@ -40,8 +40,8 @@ struct lsgcpd_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevBuf<float> X_in, Y_in, rec, part, knn_d, kap_n, gam_n;
   DevBuf<float4> xs, y4;
-  DevBuf<int> knn_i, knn_idx;
-  DevBuf<double> blk, red, trace, io;
+  DevBuf<int> knn_i, knn_idx, segtab;
+  DevBuf<double> rows, red, trace, io;
   EmState* st = nullptr;
   int* status = nullptr;
   // graph of the EM loop
@@ -54,6 +54,7 @@ struct lsgcpd_ctx {
   int t_iter_cap = 0;
   double last_timing[6] = {0, 0, 0, 0, 0, 0};
   int64_t launches = 0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
 };
 
 namespace {
@@ -191,7 +192,8 @@ lsgcpd_status reserve(lsgcpd_ctx* c, int64_t N, int64_t M, int k, const EstepPla
   cudaError_t e = cudaSuccess;
   if (grow(c->xs, n_pad) != cudaSuccess || grow(c->rec, m_pad * kPlanes) != cudaSuccess ||
       grow(c->part, estep_partial_floats(p)) != cudaSuccess ||
-      grow(c->blk, static_cast<size_t>(combine_blocks(N)) * kGlob) != cudaSuccess ||
+      grow(c->rows, static_cast<size_t>(combine_rows(N, c->num_sms)) * kGlob) != cudaSuccess ||
+      grow(c->segtab, p.table.size()) != cudaSuccess ||
       grow(c->kap_n, n_pad) != cudaSuccess || grow(c->gam_n, n_pad) != cudaSuccess ||
       grow(c->trace, static_cast<size_t>(iters > 0 ? iters : 1) * LSGCPD_TRACE_WIDTH) != cudaSuccess)
     e = cudaErrorMemoryAllocation;
@@ -345,7 +347,8 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   if (c->y4.p) cudaFree(c->y4.p);
   if (c->knn_i.p) cudaFree(c->knn_i.p);
   if (c->knn_idx.p) cudaFree(c->knn_idx.p);
-  double* db[] = {c->blk.p, c->red.p, c->trace.p, c->io.p};
+  if (c->segtab.p) cudaFree(c->segtab.p);
+  double* db[] = {c->rows.p, c->red.p, c->trace.p, c->io.p};
   for (double* p : db)
     if (p) cudaFree(p);
   if (c->st) cudaFree(c->st);
@@ -370,10 +373,12 @@ lsgcpd_status lsgcpd_set_timing(lsgcpd_ctx* c, int enable) {
   return LSGCPD_OK;
 }
 
-lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* c, double out[6]) {
+lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* c, double out[8]) {
   if (!c || !out) return LSGCPD_EINVAL;
   for (int i = 0; i < 5; ++i) out[i] = c->last_timing[i];
   out[5] = static_cast<double>(c->launches);
+  out[6] = static_cast<double>(c->h2d_bytes);
+  out[7] = static_cast<double>(c->d2h_bytes);
   return c->timing ? LSGCPD_OK : LSGCPD_EINVAL;
 }
 
@@ -443,19 +448,23 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   LSG_CUDA(launch_pack(Y, normals, alpha, M, p->include_alpha_norm, c->st, c->rec.p, plan.num_tiles, s), "pack");
   const int mode = choose_mode(p->w, sigma2, volume, M, p->include_alpha_norm ? 12.0 : 0.0);
   int64_t launches = 11;
+  LSG_CUDA(cudaMemcpyAsync(c->segtab.p, plan.table.data(), sizeof(int) * plan.table.size(),
+                           cudaMemcpyHostToDevice, s),
+           "table");
+  const int nrows = combine_rows(N, c->num_sms);
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   if (mode == 1) {
     LSG_CUDA(launch_shift(plan, c->xs.p, c->rec.p, c->st, N, c->kap_n.p, c->gam_n.p, s), "shift");
     ++launches;
   }
-  LSG_CUDA(launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p, nullptr,
+  LSG_CUDA(launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p, c->segtab.p,
                         c->status, s),
            "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  LSG_CUDA(launch_combine(plan, c->xs.p, N, c->part.p, nullptr, c->st, mode ? c->kap_n.p : nullptr,
-                          mode ? c->gam_n.p : nullptr, c->blk.p, per_n, s),
+  LSG_CUDA(launch_combine(plan, c->xs.p, N, c->part.p, c->segtab.p, c->st, mode ? c->kap_n.p : nullptr,
+                          mode ? c->gam_n.p : nullptr, c->rows.p, nrows, per_n, s),
            "combine");
-  LSG_CUDA(launch_reduce_moments(c->blk.p, combine_blocks(N), c->io.p, s), "reduce");
+  LSG_CUDA(launch_final_reduce(c->rows.p, nrows, c->io.p, nullptr, s), "reduce");
   launches += 3;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   double mom[LSGCPD_MOMENTS];
@@ -502,7 +511,7 @@ lsgcpd_status lsgcpd_mstep(lsgcpd_ctx* c, const double* moments, const double R[
   memcpy(host + 89, t, sizeof(double) * 3);
   LSG_CUDA(cudaMemcpyAsync(c->io.p, host, sizeof(host), cudaMemcpyHostToDevice, s), "copy");
   DevParams dp = dev_params(p);
-  LSG_CUDA(launch_mstep(c->io.p, 0, nullptr, dp, nullptr, c->io.p + 80, 1, s), "mstep");
+  LSG_CUDA(launch_mstep_standalone(c->io.p, dp, s), "mstep");
   LSG_CUDA(cudaMemcpyAsync(host, c->io.p, sizeof(host), cudaMemcpyDeviceToHost, s), "copy");
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
   LSG_CUDA(leave(c, stream), "stream");
@@ -576,7 +585,10 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
   }
   const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
   const int mode = choose_mode(p->w, hs.sigma2_floor, hs.V, M, l_extra);
-  const int nblk = combine_blocks(N);
+  const int nrows = combine_rows(N, c->num_sms);
+  LSG_CUDA(cudaMemcpyAsync(c->segtab.p, plan.table.data(), sizeof(int) * plan.table.size(),
+                           cudaMemcpyHostToDevice, s),
+           "table");
   if (iters > 0) {
     GraphKey key;
     key.N = N;
@@ -598,15 +610,19 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
         if (ce == cudaSuccess && mode == 1)
           ce = launch_shift(plan, c->xs.p, c->rec.p, c->st, N, c->kap_n.p, c->gam_n.p, s);
         if (ce == cudaSuccess)
-          ce = launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p, nullptr,
-                            c->status, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
+          ce = launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p,
+                            c->segtab.p, c->status, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
-          ce = launch_combine(plan, c->xs.p, N, c->part.p, nullptr, c->st, mode ? c->kap_n.p : nullptr,
-                              mode ? c->gam_n.p : nullptr, c->blk.p, nullptr, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess) ce = launch_mstep(c->blk.p, nblk, c->st, dp, c->trace.p, nullptr, 0, s);
-        if (ce == cudaSuccess && c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
+          ce = launch_combine(plan, c->xs.p, N, c->part.p, c->segtab.p, c->st, mode ? c->kap_n.p : nullptr,
+                              mode ? c->gam_n.p : nullptr, c->rows.p, nrows, nullptr, s);
+        if (ce == cudaSuccess) ce = launch_final_reduce(c->rows.p, nrows, c->io.p, c->st, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
+        if (ce == cudaSuccess) ce = launch_mstep(c->io.p, c->st, dp, c->trace.p, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
       }
       cudaError_t ee = cudaStreamEndCapture(s, &g);
       if (ce != cudaSuccess || ee != cudaSuccess) {
@@ -622,7 +638,7 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
       c->gkey = key;
     }
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * (mode ? 4 : 3);
+    launches += static_cast<int64_t>(iters) * (mode ? 5 : 4);
   }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   LSG_CUDA(cudaMemcpyAsync(&hs, c->st, sizeof(EmState), cudaMemcpyDeviceToHost, s), "copy");
@@ -634,6 +650,9 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
   LSG_CUDA(leave(c, stream), "stream");
   c->launches = launches;
+  c->h2d_bytes = (xd ? 0 : 12 * N) + (yd ? 0 : 12 * M) + static_cast<int64_t>(sizeof(int) * plan.table.size());
+  c->d2h_bytes = 2 * static_cast<int64_t>(sizeof(EmState) + sizeof(int)) +
+                 (trace && iters > 0 ? static_cast<int64_t>(sizeof(double)) * LSGCPD_TRACE_WIDTH * iters : 0);
   // result in the caller's frame: t = t_c + mu_y - R mu_x
   for (int i = 0; i < 9; ++i) out->R[i] = hs.R[i];
   for (int i = 0; i < 3; ++i)

@@ -11,7 +11,7 @@
 //   S0 = sum e, rho = sum e r, W = sum e a a^T, beta = sum e (a.r) a,
 //   D' = sum e (d + kappa_n),  kappa_n = L_n / c.
 // Folding kappa_n into the squared distance makes the shift free in the hot
-// loop; the combine subtracts kappa_n S0 in FP64.
+// loop; the combine subtracts kappa_n S0.
 //
 // Hot-loop layout (GB300):
 //  * a CTA = 4 warps; each thread owns S sources (z_n duplicated into both
@@ -25,7 +25,7 @@
 //  * work = (source block) x (target tile) units split stream-K style over a
 //    grid of (SM count x resident CTAs); a CTA flushes its FP32 partial
 //    moments at block boundaries and every seg_cap tiles, so FP32 sums stay
-//    short and the FP64 combine adds the pieces in a fixed order.
+//    short; the combine adds the pieces (compensated) in a fixed order.
 // No tensor cores: the contraction depth is 3, so the work is FP32-pipe bound.
 #include <math.h>
 
@@ -188,8 +188,8 @@ template <int S>
 __global__ void __launch_bounds__(kNW * 32, (S >= 4 ? 2 : 3))
     estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec,
                  const EmState* __restrict__ st, const float* __restrict__ kap_n,
-                 float* __restrict__ part, int* __restrict__ status, int num_tiles,
-                 long long units, int seg_cap, int segs_max) {
+                 float* __restrict__ part, const int* __restrict__ table, int* __restrict__ status,
+                 int num_tiles, long long units, int seg_cap) {
   constexpr int SB = kNW * 32 * S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tiles = reinterpret_cast<float*>(smem_raw);
@@ -271,15 +271,15 @@ __global__ void __launch_bounds__(kNW * 32, (S >= 4 ? 2 : 3))
       }
     }
     if (abort) break;
-    float* dst = part + (static_cast<size_t>(blockIdx.x) * segs_max + seg) * kMom * SB;
+    float* dst = part + static_cast<size_t>(table[blockIdx.x] + seg) * kMom * SB;
 #pragma unroll
     for (int s = 0; s < S; ++s) store_acc(dst, SB, warp * 32 * S + s * 32 + lane, acc[s]);
     ++seg;
   }
   if (abort && tid == 0) {
     // let copies still in flight land before the CTA's shared memory is released
-    for (int k = 0; k < kStages; ++k) {
-      const int j = i + 1 + k;
+    for (int k = 0; k < kStages; ++k) {  // units i .. i + kStages - 1 were issued
+      const int j = i + k;
       if (j < n_units) mbar_wait(&full[j % kStages], static_cast<uint32_t>(j / kStages) & 1u);
     }
   }
@@ -308,12 +308,11 @@ __global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __re
   const float z2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, st->tf[2])));
   const float nc = st->neg_c;
   float best = -INFINITY;
-  const int plane_of[7] = {0, 1, 2, 3, 4, 5, 12};
   for (int t = 0; t < num_tiles; ++t) {
     __syncthreads();
     for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) {
       const int p = e / kTile, j = e % kTile;
-      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + plane_of[p] * kTile + j];
+      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + (p < 6 ? p : 12) * kTile + j];
     }
     __syncthreads();
 #pragma unroll 4
@@ -336,153 +335,174 @@ __global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __re
 }
 
 // ---------------------------------------------------------------------------
-// Combine: per source, add the FP32 pieces in FP64 (fixed order), normalise
-// by S0 + gamma'_n, and reduce the FP64 global moments of the M step.
+// Combine: per source, add the FP32 pieces with compensated summation,
+// normalise by S0 + gamma'_n, and form the 76 contributions to the global
+// moments of the M step.  Contributions are reduced warp by warp in FP32 with
+// error-free transformations (TwoSum: every rounding error is carried in a
+// second FP32 word), then accumulated across warps and chunks in FP64.
 // ---------------------------------------------------------------------------
 constexpr int kCombineThreads = 256;
+constexpr int kCombineWarps = kCombineThreads / 32;
 
-// Slot range of source block b inside CTA cta (mirrors the hot kernel's segmentation).
-__device__ __forceinline__ void block_slots(long long units, long long G, int num_tiles, int seg_cap,
-                                            int cta, int b, int& first, int& count) {
-  const long long s0 = static_cast<long long>(cta) * units / G;
-  const long long s1 = static_cast<long long>(cta + 1) * units / G;
-  const long long bs = static_cast<long long>(b) * num_tiles;
-  const long long be = bs + num_tiles;
-  const long long lo = s0 > bs ? s0 : bs;
-  const long long hi = s1 < be ? s1 : be;
-  if (hi <= lo) {
-    first = 0;
-    count = 0;
-    return;
-  }
-  count = static_cast<int>((hi - lo + seg_cap - 1) / seg_cap);
-  const long long bfirst = s0 / num_tiles;
-  if (b == bfirst) {
-    first = 0;
-  } else {
-    const long long len_first = (bfirst + 1) * num_tiles - s0;
-    const long long per_full = (num_tiles + seg_cap - 1) / seg_cap;
-    first = static_cast<int>((len_first + seg_cap - 1) / seg_cap + (b - bfirst - 1) * per_full);
-  }
+struct F2 {  // unevaluated sum hi + lo
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return F2{s, e};
 }
 
-__device__ __forceinline__ long long owner_cta(long long u, long long units, long long G) {
-  return ((u + 1) * G - 1) / units;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
+// Butterfly reduction of (hi, lo) over the warp; every lane ends with the total.
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    F2 s = two_sum(v.hi, oh);
+    s.lo += v.lo + ol;
+    v = s;
+  }
   return v;
 }
 
 __global__ void __launch_bounds__(kCombineThreads)
     combine_kernel(const float4* __restrict__ xs, long long N, const float* __restrict__ part,
-                   const EmState* __restrict__ st, const float* __restrict__ kap_n,
-                   const float* __restrict__ gam_n, double* __restrict__ blk,
-                   float* __restrict__ per_n, int SB, int num_tiles, long long units, int G,
-                   int seg_cap, int segs_max) {
-  __shared__ double red[kCombineThreads / 32][kGlob];
+                   const int* __restrict__ table, const EmState* __restrict__ st,
+                   const float* __restrict__ kap_n, const float* __restrict__ gam_n,
+                   double* __restrict__ rows, float* __restrict__ per_n, int SB, int grid_e) {
+  __shared__ double acc[kCombineWarps][kGlob];
   if (st->done) return;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const long long n = static_cast<long long>(blockIdx.x) * kCombineThreads + tid;
-  const bool valid = n < N;
-
-  double m[kMom];
+  for (int j = lane; j < kGlob; j += 32) acc[warp][j] = 0.0;
+  const float kap_u = st->kap;
+  const float L_u = st->L;
+  const float gp_u = (st->log2_wodds > -INFINITY) ? 1.f : 0.f;
+  const float nc = st->neg_c;
+  const float nll_c = static_cast<float>(st->nll_const);
+  const long long stride = static_cast<long long>(gridDim.x) * kCombineThreads;
+  // every warp runs the same number of chunk iterations (whole-warp collectives)
+  for (long long base = static_cast<long long>(blockIdx.x) * kCombineThreads; base < N; base += stride) {
+    const long long n = base + tid;
+    const bool valid = n < N;
+    float m[kMom], cmp[kMom];
 #pragma unroll
-  for (int k = 0; k < kMom; ++k) m[k] = 0.0;
-  double xt0 = 0, xt1 = 0, xt2 = 0;
-  double kap = 0, gp = 0, L = 0;
-  if (valid) {
-    const int b = static_cast<int>(n / SB);
-    const int nl = static_cast<int>(n % SB);
-    const long long c0 = owner_cta(static_cast<long long>(b) * num_tiles, units, G);
-    const long long c1 = owner_cta(static_cast<long long>(b + 1) * num_tiles - 1, units, G);
-    for (long long c = c0; c <= c1; ++c) {
-      int first, count;
-      block_slots(units, G, num_tiles, seg_cap, static_cast<int>(c), b, first, count);
+    for (int k = 0; k < kMom; ++k) m[k] = cmp[k] = 0.f;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f, kap = 0.f, gp = 0.f, L = 0.f;
+    if (valid) {
+      const int b = static_cast<int>(n / SB);
+      const int nl = static_cast<int>(n - static_cast<long long>(b) * SB);
+      const int first = table[grid_e + 1 + 2 * b];
+      const int count = table[grid_e + 2 + 2 * b];
       for (int j = first; j < first + count; ++j) {
-        const float* src = part + (static_cast<size_t>(c) * segs_max + j) * kMom * SB + nl;
+        const float* src = part + static_cast<size_t>(j) * kMom * SB + nl;
 #pragma unroll
-        for (int k = 0; k < kMom; ++k) m[k] += static_cast<double>(src[static_cast<size_t>(k) * SB]);
+        for (int k = 0; k < kMom; ++k) {  // Kahan summation of the pieces
+          const float y = src[static_cast<size_t>(k) * SB] - cmp[k];
+          const float t = m[k] + y;
+          cmp[k] = (t - m[k]) - y;
+          m[k] = t;
+        }
+      }
+      const float4 x = xs[n];
+      x0 = x.x;
+      x1 = x.y;
+      x2 = x.z;
+      if (kap_n) {
+        kap = kap_n[n];
+        gp = gam_n[n];
+        L = -kap * nc;
+      } else {
+        kap = kap_u;
+        gp = gp_u;
+        L = L_u;
       }
     }
-    const float4 x = xs[n];
-    xt0 = x.x;
-    xt1 = x.y;
-    xt2 = x.z;
-    const double nc = st->neg_c;
-    if (kap_n) {
-      kap = kap_n[n];
-      gp = gam_n[n];
-      L = -kap * nc;
-    } else {
-      kap = st->kap;
-      gp = (st->log2_wodds > -INFINITY) ? 1.0 : 0.0;
-      L = st->L;
+    const float S0 = m[0];
+    const float D = m[13] - kap * S0;
+    const float denom = S0 + gp;
+    const float inv = denom > 0.f ? 1.f / denom : 0.f;
+    const float Pb = S0 * inv;
+    const float r0 = m[1] * inv, r1 = m[2] * inv, r2 = m[3] * inv;
+    const float W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv,
+                W12 = m[8] * inv, W22 = m[9] * inv;
+    const float be0 = m[10] * inv, be1 = m[11] * inv, be2 = m[12] * inv;
+    const float Dn = D * inv;
+    const float Pout = gp * inv;
+    const float nll = (valid && denom > 0.f) ? nll_c - (L * 0.6931471805599453f + logf(denom)) : 0.f;
+    if (valid && per_n) {
+      float4* o = reinterpret_cast<float4*>(per_n + n * 16);
+      o[0] = make_float4(Pb, r0, r1, r2);
+      o[1] = make_float4(W00, W01, W02, W11);
+      o[2] = make_float4(W12, W22, be0, be1);
+      o[3] = make_float4(be2, Dn, Pout, 0.f);
     }
+    const float h[3] = {r0 + be0, r1 + be1, r2 + be2};
+    const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
+    const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
+    // lane l keeps the warp totals of moments l, l + 32, l + 64 (FP64 adds stay full-warp)
+    float keep_hi[3] = {0.f, 0.f, 0.f}, keep_lo[3] = {0.f, 0.f, 0.f};
+    auto put = [&](int j, float v) {
+      const F2 r = warp_sum_f2(F2{v, 0.f});
+      if (lane == (j & 31)) {
+        keep_hi[j >> 5] = r.hi;
+        keep_lo[j >> 5] = r.lo;
+      }
+    };
+    put(0, Pb);
+    put(1, Dn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) put(2 + 4 * i + k, h[i] * xt[k]);
+    {
+      int j = 14;
+#pragma unroll
+      for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int l = k; l < 4; ++l) put(j++, A[p] * (xt[k] * xt[l]));
+    }
+    put(74, Pout);
+    put(75, nll);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (lane + 32 * i < kGlob)
+        acc[warp][lane + 32 * i] += static_cast<double>(keep_hi[i]) + static_cast<double>(keep_lo[i]);
   }
-  // normalisation
-  const double S0 = m[0];
-  const double D = m[13] - kap * S0;
-  const double denom = S0 + gp;
-  const double inv = denom > 0.0 ? 1.0 / denom : 0.0;
-  const double Pb = S0 * inv;
-  const double rho0 = m[1] * inv, rho1 = m[2] * inv, rho2 = m[3] * inv;
-  const double W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv,
-               W12 = m[8] * inv, W22 = m[9] * inv;
-  const double be0 = m[10] * inv, be1 = m[11] * inv, be2 = m[12] * inv;
-  const double Dn = D * inv;
-  const double Pout = gp * inv;
-  const double nll = valid && denom > 0.0 ? st->nll_const - (L * 0.69314718055994530942 + log(denom)) : 0.0;
-  if (valid && per_n) {
-    float* o = per_n + n * 16;
-    const double v[16] = {Pb, rho0, rho1, rho2, W00, W01, W02, W11, W12, W22, be0, be1, be2, Dn, Pout, 0.0};
-#pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = static_cast<float>(v[k]);
-  }
-  const double h[3] = {rho0 + be0, rho1 + be1, rho2 + be2};
-  const double A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
-  const double xt[4] = {xt0, xt1, xt2, valid ? 1.0 : 0.0};
-
-  // contributions, reduced warp by warp into shared memory
-  auto put = [&](int j, double v) {
-    v = warp_sum(v);
-    if (lane == 0) red[warp][j] = v;
-  };
-  put(0, Pb);
-  put(1, Dn);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) put(2 + 4 * i + k, h[i] * xt[k]);
-  {
-    int j = 14;
-#pragma unroll
-    for (int p = 0; p < 6; ++p)
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int l = k; l < 4; ++l) put(j++, A[p] * xt[k] * xt[l]);
-  }
-  put(74, Pout);
-  put(75, nll);
   __syncthreads();
   if (tid < kGlob) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kCombineThreads / 32; ++w) s += red[w][tid];
-    blk[static_cast<size_t>(blockIdx.x) * kGlob + tid] = s;
+    for (int w = 0; w < kCombineWarps; ++w) s += acc[w][tid];
+    rows[static_cast<size_t>(blockIdx.x) * kGlob + tid] = s;
   }
+}
+
+// One warp per global moment: lanes take strided rows, then a shuffle tree (FP64).
+__global__ void final_reduce_kernel(const double* __restrict__ rows, int nrows, double* __restrict__ mom,
+                                    const EmState* __restrict__ st) {
+  if (st && st->done) return;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= kGlob) return;
+  double v = 0.0;
+  for (int r = lane; r < nrows; r += 32) v += rows[static_cast<size_t>(r) * kGlob + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) mom[j] = v;
 }
 
 template <int S>
 cudaError_t launch_estep_t(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                           const float* kap_n, float* part, int* status, cudaStream_t s) {
-  estep_kernel<S><<<p.grid, kNW * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, status,
-                                                        p.num_tiles, p.units, p.seg_cap, p.segs_max);
+                           const float* kap_n, float* part, const int* table, int* status, cudaStream_t s) {
+  estep_kernel<S><<<p.grid, kNW * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, table, status,
+                                                        p.num_tiles, p.units, p.seg_cap);
   return cudaGetLastError();
 }
 
@@ -507,11 +527,11 @@ EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
   p.NW = kNW;
   p.num_tiles = static_cast<int>((M + kTile - 1) / kTile);
   p.smem_bytes = kStages * kTileBytes + kStages * sizeof(uint64_t);
-  const int cands[3] = {4, 2, 1};
   int chosen = 1;
   if (S_override == 1 || S_override == 2 || S_override == 4) {
     chosen = S_override;
   } else {
+    const int cands[3] = {4, 2, 1};
     for (int c : cands) {
       const int SB = kNW * 32 * c;
       const long long blocks = (N + SB - 1) / SB;
@@ -529,22 +549,46 @@ EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
   const long long slots = static_cast<long long>(num_sms) * resident_ctas(chosen);
   p.grid = static_cast<int>(p.units < slots ? p.units : slots);
   p.seg_cap = 64;
-  const long long per_cta = (p.units + p.grid - 1) / p.grid;
-  p.segs_max = static_cast<int>((per_cta + p.seg_cap - 1) / p.seg_cap + (per_cta + p.num_tiles - 1) / p.num_tiles + 2);
+  // slot table: replay the kernel's segmentation (same rules, host side)
+  p.table.assign(static_cast<size_t>(p.grid) + 1 + 2 * static_cast<size_t>(p.num_blocks), 0);
+  std::vector<int> first(p.num_blocks, -1), count(p.num_blocks, 0);
+  int slot = 0;
+  for (int c = 0; c < p.grid; ++c) {
+    p.table[c] = slot;
+    const long long u0 = static_cast<long long>(c) * p.units / p.grid;
+    const long long u1 = static_cast<long long>(c + 1) * p.units / p.grid;
+    long long u = u0;
+    while (u < u1) {
+      const int b = static_cast<int>(u / p.num_tiles);
+      long long e = u + p.seg_cap;
+      const long long be = static_cast<long long>(b + 1) * p.num_tiles;
+      if (e > be) e = be;
+      if (e > u1) e = u1;
+      if (first[b] < 0) first[b] = slot;
+      ++count[b];
+      ++slot;
+      u = e;
+    }
+  }
+  p.table[p.grid] = slot;
+  p.total_slots = slot;
+  for (int b = 0; b < p.num_blocks; ++b) {
+    p.table[p.grid + 1 + 2 * b] = first[b];
+    p.table[p.grid + 2 + 2 * b] = count[b];
+  }
   return p;
 }
 
 size_t estep_partial_floats(const EstepPlan& p) {
-  return static_cast<size_t>(p.grid) * p.segs_max * kMom * p.SB;
+  return static_cast<size_t>(p.total_slots) * kMom * p.SB;
 }
 
 cudaError_t launch_estep(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         const float* kap_n, float* part, int* /*part_meta*/, int* status,
-                         cudaStream_t s) {
+                         const float* kap_n, float* part, const int* table, int* status, cudaStream_t s) {
   switch (p.S) {
-    case 4: return launch_estep_t<4>(p, xs, rec, st, kap_n, part, status, s);
-    case 2: return launch_estep_t<2>(p, xs, rec, st, kap_n, part, status, s);
-    default: return launch_estep_t<1>(p, xs, rec, st, kap_n, part, status, s);
+    case 4: return launch_estep_t<4>(p, xs, rec, st, kap_n, part, table, status, s);
+    case 2: return launch_estep_t<2>(p, xs, rec, st, kap_n, part, table, status, s);
+    default: return launch_estep_t<1>(p, xs, rec, st, kap_n, part, table, status, s);
   }
 }
 
@@ -556,14 +600,25 @@ cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec,
   return cudaGetLastError();
 }
 
-int combine_blocks(int64_t N) { return static_cast<int>((N + kCombineThreads - 1) / kCombineThreads); }
+int combine_rows(int64_t N, int num_sms) {
+  const long long b = (N + kCombineThreads - 1) / kCombineThreads;
+  const long long cap = 2LL * num_sms;
+  return static_cast<int>(b < cap ? b : cap);
+}
 
 cudaError_t launch_combine(const EstepPlan& p, const float4* xs, int64_t N, const float* part,
-                           const int* /*part_meta*/, const EmState* st, const float* kap_n,
-                           const float* gam_n, double* blk, float* per_n, cudaStream_t s) {
-  combine_kernel<<<combine_blocks(N), kCombineThreads, 0, s>>>(xs, N, part, st, kap_n, gam_n, blk,
-                                                               per_n, p.SB, p.num_tiles, p.units,
-                                                               p.grid, p.seg_cap, p.segs_max);
+                           const int* table, const EmState* st, const float* kap_n, const float* gam_n,
+                           double* rows, int nrows, float* per_n, cudaStream_t s) {
+  combine_kernel<<<nrows, kCombineThreads, 0, s>>>(xs, N, part, table, st, kap_n, gam_n, rows, per_n, p.SB,
+                                                   p.grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_reduce(const double* rows, int nrows, double* mom, const EmState* st,
+                                cudaStream_t s) {
+  const int warps_per_block = 4;
+  const int blocks = (kGlob + warps_per_block - 1) / warps_per_block;
+  final_reduce_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(rows, nrows, mom, st);
   return cudaGetLastError();
 }
 

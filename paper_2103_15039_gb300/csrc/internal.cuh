@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lsg {
 
 // ---------------------------------------------------------------------------
@@ -45,6 +47,8 @@ struct EmState {
   double mu_x[3];       // source centroid
   double mu_y[3];       // target centroid
   double nll_const;     // per-source constant of -log p: -ln((1-w) (2 pi s2)^(-3/2)) at the E step
+  double log2_V;        // log2 V
+  double ln_1mw;        // ln(1 - w)
   int32_t done;         // EM finished (floor, tol or numeric failure)
   int32_t iter;         // iterations completed
   int32_t numeric_fail;
@@ -57,6 +61,21 @@ struct EmState {
   float L;              // uniform log2 shift (fixed-shift mode): log2 gamma
   float pad1;
 };
+
+// E-step constants for the current (R, t, sigma2) of the state.  The shift L
+// and the logarithms feed FP32 arithmetic only, so they are evaluated in FP32.
+__device__ inline void set_estep_constants(EmState* st) {
+  const double s2 = st->sigma2;
+  const double c = 1.4426950408889634 / (2.0 * s2);  // log2(e) / (2 s2)
+  const float lg = log2f(static_cast<float>(6.283185307179586 * s2));
+  const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
+  for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
+  for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
+  st->neg_c = static_cast<float>(-c);
+  st->L = L;
+  st->kap = static_cast<float>(static_cast<double>(L) / c);
+  st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
+}
 
 // Scalar parameters the device needs (a subset of lsgcpd_params, plus sizes).
 struct DevParams {
@@ -76,40 +95,50 @@ struct DevParams {
 
 // Launch plan of the hot E-step kernel: a stream-K style split of
 // (source block) x (target tile) units over a grid sized to the SM count.
+// A CTA flushes its partial moments into a new slot at every source-block
+// boundary and every seg_cap tiles.  Slots are numbered CTA-major, so all
+// slots of one source block are contiguous.  `table` holds, for the device:
+//   [0, grid]                first slot of every CTA (prefix sums)
+//   [grid+1, grid+1+2*blocks) (first slot, slot count) of every source block
 struct EstepPlan {
   int S;               // sources per thread
   int NW;              // warps per CTA
   int SB;              // sources per block = NW * 32 * S
   int num_blocks;      // ceil(N / SB)
   int num_tiles;       // ceil(M / kTile)
-  int64_t units;       // num_blocks * num_tiles
+  long long units;     // num_blocks * num_tiles
   int grid;            // CTAs (<= units)
   int seg_cap;         // flush after this many tiles (FP32 sums stay short)
-  int segs_max;        // partial slots per CTA
+  int total_slots;
   size_t smem_bytes;
+  std::vector<int> table;
 };
 
 // ----- kernels / launchers (estep.cu) -------------------------------------
 EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override);
 size_t estep_partial_floats(const EstepPlan& p);
 cudaError_t launch_estep(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         const float* kap_n, float* part, int* part_meta, int* status,
+                         const float* kap_n, float* part, const int* table, int* status,
                          cudaStream_t s);
 cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
                          int64_t N, float* kap_n, float* gam_n, cudaStream_t s);
-int combine_blocks(int64_t N);
+// rows of FP64 partial global moments written by the combine kernel
+int combine_rows(int64_t N, int num_sms);
 cudaError_t launch_combine(const EstepPlan& p, const float4* xs, int64_t N, const float* part,
-                           const int* part_meta, const EmState* st, const float* kap_n,
-                           const float* gam_n, double* blk, float* per_n, cudaStream_t s);
+                           const int* table, const EmState* st, const float* kap_n,
+                           const float* gam_n, double* rows, int nrows, float* per_n,
+                           cudaStream_t s);
+// Sum the rows (fixed order, FP64) into kGlob moments; one warp per moment.
+cudaError_t launch_final_reduce(const double* rows, int nrows, double* mom, const EmState* st,
+                                cudaStream_t s);
 
 // ----- M step (mstep.cu) -------------------------------------------------------
-// Reduce `nblk` partial moment rows, run the Newton M step and update the state.
-// mode_tail: 1 = full EM iteration (update state, trace, E-step constants);
-//            0 = standalone M step (write results to `out`).
-cudaError_t launch_mstep(const double* blk, int nblk, EmState* st, const DevParams& dp,
-                         double* trace, double* out, int standalone, cudaStream_t s);
-// Sum `nblk` partial moment rows into `out` (kGlob doubles), fixed order.
-cudaError_t launch_reduce_moments(const double* blk, int nblk, double* out, cudaStream_t s);
+// Newton M step from the kGlob global moments `mom` and the state update.
+cudaError_t launch_mstep(const double* mom, EmState* st, const DevParams& dp, double* trace,
+                         cudaStream_t s);
+// Standalone M step: io[0..75] moments, io[80..91] starting pose (R, t);
+// results R (9), t (3), sigma2, Q, newton steps, damped, halvings at io[96..112].
+cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s);
 
 // ----- preprocessing / initialisation (prep.cu) ------------------------------
 int stats_blocks(int64_t n);

@@ -1,24 +1,33 @@
-// M step of LSG-CPD (Sec. 3.5, Eqs. (11)-(13)) and the sigma^2 update, in FP64,
-// from the global moments of one E step.
+// M step of LSG-CPD (Sec. 3.5, Eqs. (11)-(13)) and the sigma^2 update, from
+// the global moments of one E step.
 //
-// With the posteriors fixed, sum_m P_mn d_mn is a quadratic function of the
-// moved source point, and the moved point z' = g_old Delta x is affine in
-// U = [Delta_R - I | Delta_t] (3x4).  Writing x~ = [x; 1],
-//   Q_d(Delta) = sum_n D_n + 2 <H1', U> + sum_{i,k,j,l} U_ik U_jl B^{kl}_ij,
-//   H1' = R_old^T sum_n h_n x~_n^T,   B^{kl} = R_old^T (sum_n A_n x~_nk x~_nl) R_old,
-// exactly (h_n = rho_n + beta_n, A_n = Pbar_n I + W_n).  The Newton iteration
-// of Eq. (13) on SE(3) (right perturbation Delta o exp(xi^), basis order
-// rotations x, y, z then translations) needs the gradient and the symmetrised
-// Hessian (H + H^T)/2 of xi -> Q_d(Delta o exp(xi^)) at xi = 0, which follow
-// from the first and second derivatives of U(xi):
-//   dU/dw_a = [Delta_R [e_a]x | 0],  dU/dv_a = [0 | Delta_R e_a],
-//   d2U/dw_a dw_b = [Delta_R ([e_a]x[e_b]x + [e_b]x[e_a]x)/2 | 0],
-//   d2U/dw_a dv_b = [0 | Delta_R [e_a]x e_b / 2].
-// So the whole inner Newton loop is O(1) work on 76 numbers, independent of N and M.
-// Step rule: xi = -(H_s)^{-1} grad by Cholesky; if H_s is not positive definite
-// it is damped by mu I (mu from 1e-6 tr/6, x10); a step that raises Q_d is halved
-// up to 10 times; stop when |xi| < newton_tol, after newton_max steps, or when no
-// halving lowers Q_d.  sigma^2 = Q_d(g_new) / (3 N_P) (dQ/dsigma^2 = 0 of Eq. (6)).
+// With the posteriors fixed, sum_m P_mn d_mn is an exact quadratic function
+// of the moved source point, and the moved point is affine in T = [R | t]
+// (3x4).  With x~ = [x; 1] and the transform T_o used by the E step,
+//   Q_d(T) = SD + 2 <H1, T - T_o> + <T - T_o, G (T - T_o)>,
+//   H1 = sum_n h_n x~_n^T,  G_(ik),(jl) = A^{kl}_ij = sum_n A_n,ij x~_nk x~_nl,
+// (h_n = rho_n + beta_n, A_n = Pbar_n I + W_n), so the inner Newton loop of
+// Eq. (13) costs O(1) per step, independent of N and M.
+//
+// Newton on SE(3): right perturbation T o exp(xi^), basis order rotations
+// about x, y, z then translations.  With M1 = H1 + G (T - T_o),
+// N = R^T M1[:, :3], m = R^T M1[:, 3] and C^{kl} = R^T A^{kl} R:
+//   grad_rot a  = 2 <N, [e_a]x>,             grad_tr c = 2 m_c
+//   H_rot a,rot b = 2 sum eps_aik eps_bjl C^{kl}_ij + N_ab + N_ba - 2 delta_ab tr N
+//   H_rot a,tr c  = -2 sum eps_aik C^{k3}_ic + m . (e_a x e_c)
+//   H_tr c,tr d   = 2 C^{33}_cd
+// which is the symmetrised Hessian (H + H^T)/2 of Eq. (12) at the current iterate.
+// Step rule (same as the FP64 reference): xi = -(H_s)^{-1} grad; if H_s is not
+// positive definite it is damped by mu I (mu = 1e-6 tr/6, x10); a step that
+// raises Q_d is halved up to 10 times; stop when |xi| < newton_tol, after
+// newton_max steps, or when no halving lowers Q_d.
+//
+// Precision (GB300 issues one FP64 warp instruction per ~64 cycles per SM
+// sub-partition): the model, the residual M1, the objective change
+// dQ = 2 <M1, D> + <D, G D> of a trial step D and the transform are FP64 and
+// computed lane-parallel; only the 6x6 solve for the Newton direction runs in
+// FP32 (LDL^T).  An inexact direction only changes the path, not the fixed
+// point, which is set by the FP64 residual (iterative refinement).
 #include <math.h>
 
 #include "internal.cuh"
@@ -26,387 +35,399 @@
 namespace lsg {
 namespace {
 
-constexpr int kRedThreads = 256;
+constexpr int kMThreads = 128;
 
-struct NewtonOut {
-  double dR[9], dt[3];
+struct Shared {
+  double SD, NP;
+  double H1[12];
+  double A[10][6];  // A^{q}, q = xt pair (00,01,02,03,11,12,13,22,23,33), entries (00,01,02,11,12,22)
+  double R[9], t[3];
+  double Ro[9], to[3];
+  double M1[12];
   double Q;
+  double C[10][9];
+  double NM[12];
+  double gH[27];   // grad (6) then the upper triangle of H_s (21)
+  double xi[6];
+  double coef[3];  // exp coefficients
+  double wv[6];    // scaled step
+  double E[9], Vv[3];
+  double Tc[12], dl[12], Gd[12];
+  double dQ;
   int iters, damped, halvings;
+  int go;          // loop control
+  int accepted;
 };
 
-// Q model data
-struct QModel {
-  double SD;
-  double H1[3][4];
-  double B[4][4][3][3];  // B[k][l][i][j]
-};
-
-__device__ void build_model(const double* mom, const double* Ro, QModel& q) {
-  q.SD = mom[1];
-  double H1[3][4];
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) H1[i][k] = mom[2 + 4 * i + k];
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) {
-      double s = 0;
-      for (int a = 0; a < 3; ++a) s += Ro[3 * a + i] * H1[a][k];
-      q.H1[i][k] = s;
-    }
-  // xt pair index of (k, l), k <= l
-  int qi = 0;
-  for (int k = 0; k < 4; ++k)
-    for (int l = k; l < 4; ++l, ++qi) {
-      double A[3][3];
-      const double* g = mom + 14;  // g[p * 10 + qi], p = (00,01,02,11,12,22)
-      A[0][0] = g[0 * 10 + qi];
-      A[0][1] = A[1][0] = g[1 * 10 + qi];
-      A[0][2] = A[2][0] = g[2 * 10 + qi];
-      A[1][1] = g[3 * 10 + qi];
-      A[1][2] = A[2][1] = g[4 * 10 + qi];
-      A[2][2] = g[5 * 10 + qi];
-      double T[3][3], Bm[3][3];
-      for (int a = 0; a < 3; ++a)
-        for (int j = 0; j < 3; ++j) {
-          double s = 0;
-          for (int b = 0; b < 3; ++b) s += A[a][b] * Ro[3 * b + j];
-          T[a][j] = s;
-        }
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-          double s = 0;
-          for (int a = 0; a < 3; ++a) s += Ro[3 * a + i] * T[a][j];
-          Bm[i][j] = s;
-        }
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-          q.B[k][l][i][j] = Bm[i][j];
-          q.B[l][k][i][j] = Bm[i][j];
-        }
-    }
+__device__ __forceinline__ int pair_q(int k, int l) {
+  if (k > l) {
+    const int t = k;
+    k = l;
+    l = t;
+  }
+  // (0,0)0 (0,1)1 (0,2)2 (0,3)3 (1,1)4 (1,2)5 (1,3)6 (2,2)7 (2,3)8 (3,3)9
+  return k == 0 ? l : (k == 1 ? 3 + l : (k == 2 ? 5 + l : 9));
 }
 
-// GU[i][k] = sum_{j,l} B[k][l][i][j] U[j][l]
-__device__ void apply_G(const QModel& q, const double U[3][4], double GU[3][4]) {
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) {
-      double s = 0;
-      for (int j = 0; j < 3; ++j)
-        for (int l = 0; l < 4; ++l) s += q.B[k][l][i][j] * U[j][l];
-      GU[i][k] = s;
-    }
+__device__ __forceinline__ int sym_p(int i, int j) {
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  return i == 0 ? j : (i == 1 ? 2 + j : 5);
 }
 
-__device__ double frob(const double A[3][4], const double B[3][4]) {
-  double s = 0;
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 4; ++k) s += A[i][k] * B[i][k];
-  return s;
+__device__ __forceinline__ double Aent(const Shared& s, int q, int i, int j) { return s.A[q][sym_p(i, j)]; }
+__device__ __forceinline__ double Cent(const Shared& s, int k, int l, int i, int j) {
+  return s.C[pair_q(k, l)][3 * i + j];
 }
 
-__device__ double q_value(const QModel& q, const double U[3][4]) {
-  double GU[3][4];
-  apply_G(q, U, GU);
-  return q.SD + 2.0 * frob(q.H1, U) + frob(U, GU);
+// Levi-Civita symbol for indices in {0, 1, 2}
+__device__ __forceinline__ double eps3(int a, int b, int c) {
+  if (a == b || b == c || a == c) return 0.0;
+  return ((b - a + 3) % 3 == 1) ? 1.0 : -1.0;
 }
 
-__device__ void make_U(const double dR[9], const double dt[3], double U[3][4]) {
-  for (int i = 0; i < 3; ++i) {
-    for (int k = 0; k < 3; ++k) U[i][k] = dR[3 * i + k] - (i == k ? 1.0 : 0.0);
-    U[i][3] = dt[i];
+__device__ void load_model(Shared& s, const double* mom) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s.NP = mom[0];
+    s.SD = mom[1];
+  }
+  if (tid < 12) s.H1[tid] = mom[2 + tid];
+  if (tid < 60) {
+    const int p = tid / 10, q = tid % 10;  // moments are ordered A pair major, xt pair minor
+    s.A[q][p] = mom[14 + tid];
   }
 }
 
-// hat(e_a) applied: ([e_a]x)[r][c]
-__device__ __forceinline__ double hat_e(int a, int r, int c) {
-  // [e]_x = [[0,-e2,e1],[e2,0,-e0],[-e1,e0,0]]
-  if (a == 0) return (r == 2 && c == 1) ? 1.0 : ((r == 1 && c == 2) ? -1.0 : 0.0);
-  if (a == 1) return (r == 0 && c == 2) ? 1.0 : ((r == 2 && c == 0) ? -1.0 : 0.0);
-  return (r == 1 && c == 0) ? 1.0 : ((r == 0 && c == 1) ? -1.0 : 0.0);
-}
-
-// closed-form exponential of se(3): xi = (w, v) -> (R, t)
-__device__ void se3_exp_dev(const double xi[6], double R[9], double t[3]) {
-  const double w0 = xi[0], w1 = xi[1], w2 = xi[2];
-  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-  const double th = sqrt(th2);
-  double a, b, c;
-  if (th < 1e-4) {
-    a = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-    b = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-    c = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
-  } else {
-    const double sn = sin(th), cs = cos(th);
-    a = sn / th;
-    b = (1.0 - cs) / th2;
-    c = (th - sn) / (th2 * th);
-  }
-  const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-  double K2[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
-  double V[9];
-  for (int i = 0; i < 9; ++i) {
-    const double I = (i % 4 == 0) ? 1.0 : 0.0;
-    R[i] = I + a * K[i] + b * K2[i];
-    V[i] = I + b * K[i] + c * K2[i];
-  }
-  for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * xi[3] + V[3 * i + 1] * xi[4] + V[3 * i + 2] * xi[5];
-}
-
-__device__ bool cholesky_solve6(const double S[36], const double b[6], double x[6]) {
-  double L[36];
-  for (int i = 0; i < 36; ++i) L[i] = 0.0;
-  for (int i = 0; i < 6; ++i)
-    for (int j = 0; j <= i; ++j) {
-      double s = S[6 * i + j];
-      for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
-      if (i == j) {
-        if (!(s > 0.0)) return false;
-        L[6 * i + i] = sqrt(s);
-      } else {
-        L[6 * i + j] = s / L[6 * j + j];
-      }
+// FP32 LDL^T solve of the symmetric 6x6 H x = b; false if a pivot is not positive.
+__device__ bool ldl_solve6(const float H[36], const float b[6], float x[6]) {
+  float L[36], D[6];
+  for (int j = 0; j < 6; ++j) {
+    float d = H[7 * j];
+    for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k] * D[k];
+    if (!(d > 0.f)) return false;
+    D[j] = d;
+    const float inv = 1.f / d;
+    for (int i = j + 1; i < 6; ++i) {
+      float v = H[6 * i + j];
+      for (int k = 0; k < j; ++k) v -= L[6 * i + k] * L[6 * j + k] * D[k];
+      L[6 * i + j] = v * inv;
     }
-  double y[6];
+  }
+  float y[6];
   for (int i = 0; i < 6; ++i) {
-    double s = b[i];
-    for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
-    y[i] = s / L[6 * i + i];
+    float v = b[i];
+    for (int k = 0; k < i; ++k) v -= L[6 * i + k] * y[k];
+    y[i] = v;
   }
   for (int i = 5; i >= 0; --i) {
-    double s = y[i];
-    for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
-    x[i] = s / L[6 * i + i];
+    float v = y[i] / D[i];
+    for (int k = i + 1; k < 6; ++k) v -= L[6 * k + i] * x[k];
+    x[i] = v;
   }
   return true;
 }
 
-__device__ void newton(const QModel& q, int newton_max, double newton_tol, NewtonOut& o) {
-  for (int i = 0; i < 9; ++i) o.dR[i] = (i % 4 == 0) ? 1.0 : 0.0;
-  o.dt[0] = o.dt[1] = o.dt[2] = 0.0;
-  o.Q = q.SD;
-  o.iters = o.damped = o.halvings = 0;
+// Newton loop on the model in shared memory; T starts at (s.R, s.t) == (s.Ro, s.to).
+__device__ void newton(Shared& s, int newton_max, double newton_tol) {
+  const int tid = threadIdx.x;
+  if (tid < 12) s.M1[tid] = s.H1[tid];
+  if (tid == 0) {
+    s.Q = s.SD;
+    s.iters = s.damped = s.halvings = 0;
+    s.go = 1;
+  }
+  __syncthreads();
   for (int it = 0; it < newton_max; ++it) {
-    double U[3][4], GU[3][4], M1[3][4];
-    make_U(o.dR, o.dt, U);
-    apply_G(q, U, GU);
-    for (int i = 0; i < 3; ++i)
-      for (int k = 0; k < 4; ++k) M1[i][k] = q.H1[i][k] + GU[i][k];
-    double Ua[6][3][4];
-    for (int a = 0; a < 6; ++a)
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) {
-          double v = 0.0;
-          if (a < 3) {
-            if (k < 3)
-              for (int j = 0; j < 3; ++j) v += o.dR[3 * i + j] * hat_e(a, j, k);
-          } else if (k == 3) {
-            v = o.dR[3 * i + (a - 3)];
-          }
-          Ua[a][i][k] = v;
-        }
-    double grad[6], Hs[36];
-    double GUa[6][3][4];
-    for (int a = 0; a < 6; ++a) {
-      grad[a] = 2.0 * frob(M1, Ua[a]);
-      apply_G(q, Ua[a], GUa[a]);
+    // --- C^{kl} = R^T A^{kl} R (60 unique entries) and N, m = R^T M1 ---
+    if (tid < 60) {
+      const int q = tid / 6, p = tid % 6;
+      const int i = p < 3 ? 0 : (p < 5 ? 1 : 2);
+      const int j = p < 3 ? p : (p < 5 ? p - 2 : 2);
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) v += s.R[3 * a + i] * Aent(s, q, a, b) * s.R[3 * b + j];
+      s.C[q][3 * i + j] = v;
+      s.C[q][3 * j + i] = v;
+    } else if (tid >= 64 && tid < 76) {
+      const int e = tid - 64, i = e / 4, k = e % 4;
+      s.NM[e] = s.R[i] * s.M1[k] + s.R[3 + i] * s.M1[4 + k] + s.R[6 + i] * s.M1[8 + k];
     }
-    for (int a = 0; a < 6; ++a)
-      for (int b = a; b < 6; ++b) {
-        double h = 2.0 * frob(Ua[a], GUa[b]);
-        double sec = 0.0;
-        if (a < 3 && b < 3) {
-          // Delta_R (hat_a hat_b + hat_b hat_a) / 2 in the rotation block
+    __syncthreads();
+    // --- gradient (6) and the upper triangle of H_s (21) ---
+    if (tid < 27) {
+      double v = 0.0;
+      if (tid < 6) {
+        const int a = tid;
+        if (a < 3) {
+          const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+          v = 2.0 * (s.NM[4 * a2 + a1] - s.NM[4 * a1 + a2]);
+        } else {
+          v = 2.0 * s.NM[4 * (a - 3) + 3];
+        }
+      } else {
+        int e = tid - 6, a = 0;
+        while (e >= 6 - a) {
+          e -= 6 - a;
+          ++a;
+        }
+        const int b = a + e;
+        if (b < 3) {  // rotation - rotation
+          double gn = 0.0;
           for (int i = 0; i < 3; ++i)
             for (int k = 0; k < 3; ++k) {
-              double s = 0.0;
-              for (int j = 0; j < 3; ++j) {
-                double Sjk = 0.0;
-                for (int m = 0; m < 3; ++m)
-                  Sjk += 0.5 * (hat_e(a, j, m) * hat_e(b, m, k) + hat_e(b, j, m) * hat_e(a, m, k));
-                s += o.dR[3 * i + j] * Sjk;
-              }
-              sec += M1[i][k] * s;
+              const double ea = eps3(a, i, k);
+              if (ea == 0.0) continue;
+              for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                  const double eb = eps3(b, j, l);
+                  if (eb != 0.0) gn += ea * eb * Cent(s, k, l, i, j);
+                }
             }
-        } else if (a < 3 && b >= 3) {
-          for (int i = 0; i < 3; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < 3; ++j) s += o.dR[3 * i + j] * 0.5 * hat_e(a, j, b - 3);
-            sec += M1[i][3] * s;
+          const double trN = s.NM[0] + s.NM[5] + s.NM[10];
+          v = 2.0 * gn + s.NM[4 * a + b] + s.NM[4 * b + a] - (a == b ? 2.0 * trN : 0.0);
+        } else if (a < 3) {  // rotation a - translation c
+          const int c = b - 3;
+          double gn = 0.0;
+          for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+              const double ea = eps3(a, i, k);
+              if (ea != 0.0) gn -= ea * Cent(s, k, 3, i, c);
+            }
+          double sec = 0.0;
+          if (c != a) {
+            const int i = 3 - a - c;
+            sec = eps3(a, c, i) * s.NM[4 * i + 3];
           }
+          v = 2.0 * gn + sec;
+        } else {  // translation - translation
+          v = 2.0 * Cent(s, 3, 3, a - 3, b - 3);
         }
-        h += 2.0 * sec;
-        Hs[6 * a + b] = h;
-        Hs[6 * b + a] = h;
       }
-    double mg[6], xi[6];
-    for (int a = 0; a < 6; ++a) mg[a] = -grad[a];
-    if (!cholesky_solve6(Hs, mg, xi)) {
-      double tr = 0.0;
-      for (int a = 0; a < 6; ++a) tr += fabs(Hs[7 * a]);
-      double mu = 1e-6 * (tr > 0.0 ? tr / 6.0 : 1.0);
-      bool ok = false;
-      for (int k = 0; k < 40 && !ok; ++k, mu *= 10.0) {
-        double D[36];
-        for (int e = 0; e < 36; ++e) D[e] = Hs[e];
-        for (int a = 0; a < 6; ++a) D[7 * a] += mu;
-        ok = cholesky_solve6(D, mg, xi);
-      }
-      ++o.damped;
-      if (!ok) break;
+      s.gH[tid] = v;
     }
-    ++o.iters;
-    double step = 1.0;
-    bool accepted = false;
-    double nx = 0.0;
-    for (int bt = 0; bt <= 10; ++bt, step *= 0.5) {
-      double s[6], eR[9], et[3], cR[9], ct[3];
-      for (int a = 0; a < 6; ++a) s[a] = step * xi[a];
-      se3_exp_dev(s, eR, et);
-      for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j)
-          cR[3 * i + j] = o.dR[3 * i] * eR[j] + o.dR[3 * i + 1] * eR[3 + j] + o.dR[3 * i + 2] * eR[6 + j];
-        ct[i] = o.dR[3 * i] * et[0] + o.dR[3 * i + 1] * et[1] + o.dR[3 * i + 2] * et[2] + o.dt[i];
+    __syncthreads();
+    // --- Newton direction (FP32 LDL^T, damped if not positive definite) ---
+    if (tid == 0) {
+      float Hf[36], mg[6], x[6];
+      int e = 6;
+      for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b, ++e) {
+          Hf[6 * a + b] = static_cast<float>(s.gH[e]);
+          Hf[6 * b + a] = Hf[6 * a + b];
+        }
+      for (int a = 0; a < 6; ++a) mg[a] = static_cast<float>(-s.gH[a]);
+      bool ok = ldl_solve6(Hf, mg, x);
+      if (!ok) {
+        float tr = 0.f;
+        for (int a = 0; a < 6; ++a) tr += fabsf(Hf[7 * a]);
+        float mu = 1e-6f * (tr > 0.f ? tr / 6.f : 1.f);
+        for (int k = 0; k < 40 && !ok; ++k, mu *= 10.f) {
+          float Dm[36];
+          for (int q = 0; q < 36; ++q) Dm[q] = Hf[q];
+          for (int a = 0; a < 6; ++a) Dm[7 * a] += mu;
+          ok = ldl_solve6(Dm, mg, x);
+        }
+        ++s.damped;
       }
-      double Uc[3][4];
-      make_U(cR, ct, Uc);
-      const double Qc = q_value(q, Uc);
-      if (Qc <= o.Q) {
-        for (int e = 0; e < 9; ++e) o.dR[e] = cR[e];
-        for (int e = 0; e < 3; ++e) o.dt[e] = ct[e];
-        o.Q = Qc;
-        accepted = true;
-        for (int a = 0; a < 6; ++a) nx += s[a] * s[a];
-        nx = sqrt(nx);
+      if (!ok) {
+        s.go = 0;
+      } else {
+        ++s.iters;
+        for (int a = 0; a < 6; ++a) s.xi[a] = x[a];
+      }
+      s.accepted = 0;
+    }
+    __syncthreads();
+    if (!s.go) break;
+    // --- backtracking on the exact FP64 change of Q_d ---
+    double step = 1.0;
+    for (int bt = 0; bt <= 10; ++bt, step *= 0.5) {
+      if (tid == 0) {
+        double w[3], v[3];
+        for (int a = 0; a < 3; ++a) {
+          w[a] = step * s.xi[a];
+          v[a] = step * s.xi[3 + a];
+        }
+        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        double A, B, Cc;  // sin(th)/th, (1 - cos th)/th^2, (th - sin th)/th^3
+        if (th2 < 1e-8) {
+          A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
+          B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
+          Cc = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+        } else {
+          const double th = sqrt(th2);
+          double sn, cs;
+          sincos(th, &sn, &cs);
+          A = sn / th;
+          B = (1.0 - cs) / th2;
+          Cc = (th - sn) / (th2 * th);
+        }
+        s.coef[0] = A;
+        s.coef[1] = B;
+        s.coef[2] = Cc;
+        for (int a = 0; a < 3; ++a) {
+          s.wv[a] = w[a];
+          s.wv[3 + a] = v[a];
+        }
+      }
+      __syncthreads();
+      // E = I + A W + B W^2 and V v = v + B W v + C W^2 v with W = [w]x, W^2 = w w^T - th^2 I
+      if (tid < 9) {
+        const int k = tid / 3, j = tid % 3;
+        const double* w = s.wv;
+        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const double Wkj = -(eps3(k, j, 0) * w[0] + eps3(k, j, 1) * w[1] + eps3(k, j, 2) * w[2]);
+        const double W2kj = w[k] * w[j] - (k == j ? th2 : 0.0);
+        s.E[tid] = (k == j ? 1.0 : 0.0) + s.coef[0] * Wkj + s.coef[1] * W2kj;
+      } else if (tid >= 32 && tid < 35) {
+        const int i = tid - 32;
+        const double* w = s.wv;
+        const double* v = s.wv + 3;
+        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+        const double Wv = w[i1] * v[i2] - w[i2] * v[i1];  // (w x v)_i
+        const double W2v = w[i] * (w[0] * v[0] + w[1] * v[1] + w[2] * v[2]) - th2 * v[i];
+        s.Vv[i] = v[i] + s.coef[1] * Wv + s.coef[2] * W2v;
+      }
+      __syncthreads();
+      if (tid < 12) {  // candidate T o exp(step xi) and the difference D = T_c - T
+        const int i = tid / 4, k = tid % 4;
+        double v;
+        if (k < 3)
+          v = s.R[3 * i] * s.E[k] + s.R[3 * i + 1] * s.E[3 + k] + s.R[3 * i + 2] * s.E[6 + k];
+        else
+          v = s.R[3 * i] * s.Vv[0] + s.R[3 * i + 1] * s.Vv[1] + s.R[3 * i + 2] * s.Vv[2] + s.t[i];
+        s.Tc[tid] = v;
+        s.dl[tid] = v - (k < 3 ? s.R[3 * i + k] : s.t[i]);
+      }
+      __syncthreads();
+      if (tid < 32) {  // G D and dQ = 2 <M1, D> + <D, G D>
+        double dq = 0.0;
+        if (tid < 12) {
+          const int i = tid / 4, k = tid % 4;
+          double g = 0.0;
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) g += Aent(s, pair_q(k, l), i, j) * s.dl[4 * j + l];
+          s.Gd[tid] = g;
+          dq = s.dl[tid] * (2.0 * s.M1[tid] + g);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, o);
+        if (tid == 0) s.dQ = dq;
+      }
+      __syncthreads();
+      const bool acc = s.dQ <= 0.0;
+      if (acc) {
+        if (tid < 12) {
+          const int i = tid / 4, k = tid % 4;
+          if (k < 3)
+            s.R[3 * i + k] = s.Tc[tid];
+          else
+            s.t[i] = s.Tc[tid];
+          s.M1[tid] += s.Gd[tid];
+        }
+        if (tid == 0) {
+          s.Q += s.dQ;
+          s.accepted = 1;
+        }
+        __syncthreads();
         break;
       }
-      ++o.halvings;
+      if (tid == 0) ++s.halvings;
+      __syncthreads();
     }
-    if (!accepted || nx < newton_tol) break;
+    if (tid == 0) {
+      double nx = 0.0;
+      for (int a = 0; a < 6; ++a) nx += s.wv[a] * s.wv[a];
+      if (!s.accepted || sqrt(nx) < newton_tol) s.go = 0;
+    }
+    __syncthreads();
+    if (!s.go) break;
   }
 }
 
-// Sum the partial moment rows (fixed order: deterministic) into mom[kGlob].
-__device__ void reduce_rows(const double* blk, int nblk, double* part /*[8][kGlob]*/, double* mom) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = blockDim.x >> 5;
-  for (int c = lane; c < kGlob; c += 32) {
-    double s = 0.0;
-    for (int r = warp; r < nblk; r += nw) s += blk[static_cast<size_t>(r) * kGlob + c];
-    part[warp * kGlob + c] = s;
-  }
-  __syncthreads();
-  if (tid < kGlob) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += part[w * kGlob + tid];
-    mom[tid] = s;
-  }
-  __syncthreads();
-}
-
-__device__ void set_constants(EmState* st, double w) {
-  const double s2 = st->sigma2;
-  const double c = 1.4426950408889634 / (2.0 * s2);  // log2(e) / (2 s2)
-  const double L = st->log2_wodds + 1.5 * log2(2.0 * 3.14159265358979323846 * s2) - log2(st->V);
-  for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
-  for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
-  st->neg_c = static_cast<float>(-c);
-  st->L = static_cast<float>(L);
-  st->kap = static_cast<float>(L / c);
-  st->nll_const = -log1p(-w) + 1.5 * log(2.0 * 3.14159265358979323846 * s2);
-}
-
-__global__ void __launch_bounds__(kRedThreads) mstep_em_kernel(const double* __restrict__ blk, int nblk,
-                                                                EmState* __restrict__ st, DevParams dp,
-                                                                double* __restrict__ trace) {
-  __shared__ double part[(kRedThreads / 32) * kGlob];
-  __shared__ double mom[kGlob];
+__global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ mom,
+                                                              EmState* __restrict__ st, DevParams dp,
+                                                              double* __restrict__ trace) {
+  __shared__ Shared s;
   if (st->done) return;
-  reduce_rows(blk, nblk, part, mom);
-  if (threadIdx.x != 0) return;
-  const double NP = mom[0];
-  if (!(NP > 0.0)) {
-    st->numeric_fail = 1;
-    st->done = 1;
+  const int tid = threadIdx.x;
+  load_model(s, mom);
+  if (tid < 9) {
+    s.R[tid] = s.Ro[tid] = st->R[tid];
+  } else if (tid < 12) {
+    s.t[tid - 9] = s.to[tid - 9] = st->t[tid - 9];
+  }
+  __syncthreads();
+  if (!(s.NP > 0.0)) {
+    if (tid == 0) {
+      st->numeric_fail = 1;
+      st->done = 1;
+    }
     return;
   }
-  QModel q;
-  build_model(mom, st->R, q);
-  NewtonOut o;
-  newton(q, dp.newton_max, dp.newton_tol, o);
-  double Rn[9], tn[3];
+  newton(s, dp.newton_max, dp.newton_tol);
+  if (tid != 0) return;
+  // motion of this iteration in the caller's frame (diagnostic, FP32 angle)
+  double fro = 0.0, dtr2 = 0.0;
+  for (int i = 0; i < 9; ++i) fro += (s.R[i] - s.Ro[i]) * (s.R[i] - s.Ro[i]);
   for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j)
-      Rn[3 * i + j] = st->R[3 * i] * o.dR[j] + st->R[3 * i + 1] * o.dR[3 + j] + st->R[3 * i + 2] * o.dR[6 + j];
-    tn[i] = st->R[3 * i] * o.dt[0] + st->R[3 * i + 1] * o.dt[1] + st->R[3 * i + 2] * o.dt[2] + st->t[i];
+    double d = s.t[i] - s.to[i];
+    for (int j = 0; j < 3; ++j) d -= (s.R[3 * i + j] - s.Ro[3 * i + j]) * st->mu_x[j];
+    dtr2 += d * d;
   }
-  // motion in the caller's frame: rotation angle of Delta_R and the change of
-  // t_raw = t + mu_y - R mu_x, relative to the target diagonal
-  double fro = 0.0;
-  for (int i = 0; i < 9; ++i) {
-    const double d = o.dR[i] - ((i % 4 == 0) ? 1.0 : 0.0);
-    fro += d * d;
-  }
-  const double ang = 2.0 * asin(fmin(1.0, sqrt(fro) / (2.0 * sqrt(2.0))));
-  double dtr2 = 0.0;
-  for (int i = 0; i < 3; ++i) {
-    const double to = st->t[i] - (st->R[3 * i] * st->mu_x[0] + st->R[3 * i + 1] * st->mu_x[1] + st->R[3 * i + 2] * st->mu_x[2]);
-    const double tw = tn[i] - (Rn[3 * i] * st->mu_x[0] + Rn[3 * i + 1] * st->mu_x[1] + Rn[3 * i + 2] * st->mu_x[2]);
-    dtr2 += (tw - to) * (tw - to);
-  }
-  const double motion = fmax(ang, sqrt(dtr2) / (st->diag > 0 ? st->diag : 1.0));
-  const double s2 = o.Q / (3.0 * NP);
+  const float ang = 2.f * asinf(fminf(1.f, sqrtf(static_cast<float>(fro)) * 0.35355339f));
+  const float motion = fmaxf(ang, sqrtf(static_cast<float>(dtr2)) / static_cast<float>(st->diag > 0 ? st->diag : 1.0));
+  const double s2 = s.Q / (3.0 * s.NP);
   const bool at_floor = !(s2 > st->sigma2_floor);
-  for (int i = 0; i < 9; ++i) st->R[i] = Rn[i];
-  for (int i = 0; i < 3; ++i) st->t[i] = tn[i];
+  for (int i = 0; i < 9; ++i) st->R[i] = s.R[i];
+  for (int i = 0; i < 3; ++i) st->t[i] = s.t[i];
   st->sigma2 = at_floor ? st->sigma2_floor : s2;
   const int it = st->iter;
   if (trace) {
     double* tr = trace + static_cast<size_t>(it) * 8;
     tr[0] = st->sigma2;
-    tr[1] = NP;
-    tr[2] = o.Q;
-    tr[3] = o.iters;
-    tr[4] = o.damped;
+    tr[1] = s.NP;
+    tr[2] = s.Q;
+    tr[3] = s.iters;
+    tr[4] = s.damped;
     tr[5] = motion;
     tr[6] = mom[75];
     tr[7] = mom[74];
   }
   st->iter = it + 1;
   if (at_floor || (dp.tol > 0.0 && motion < dp.tol) || st->iter >= dp.max_iters) st->done = 1;
-  set_constants(st, dp.w);
+  set_estep_constants(st);
 }
 
-// Standalone M step: moments and the starting pose are given; results go to `out`:
-// R (9), t (3), sigma2, Q, newton_iters, damped, halvings.
-__global__ void mstep_standalone_kernel(const double* __restrict__ mom, const double* __restrict__ pose,
-                                        DevParams dp, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  QModel q;
-  build_model(mom, pose, q);
-  NewtonOut o;
-  newton(q, dp.newton_max, dp.newton_tol, o);
-  const double* R = pose;
-  const double* t = pose + 9;
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j)
-      out[3 * i + j] = R[3 * i] * o.dR[j] + R[3 * i + 1] * o.dR[3 + j] + R[3 * i + 2] * o.dR[6 + j];
-    out[9 + i] = R[3 * i] * o.dt[0] + R[3 * i + 1] * o.dt[1] + R[3 * i + 2] * o.dt[2] + t[i];
+__global__ void __launch_bounds__(kMThreads) mstep_standalone_kernel(double* __restrict__ io, DevParams dp) {
+  __shared__ Shared s;
+  const int tid = threadIdx.x;
+  load_model(s, io);
+  if (tid < 9) {
+    s.R[tid] = s.Ro[tid] = io[80 + tid];
+  } else if (tid < 12) {
+    s.t[tid - 9] = s.to[tid - 9] = io[80 + tid];
   }
-  out[12] = mom[0] > 0.0 ? o.Q / (3.0 * mom[0]) : 0.0;
-  out[13] = o.Q;
-  out[14] = o.iters;
-  out[15] = o.damped;
-  out[16] = o.halvings;
-}
-
-__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* __restrict__ blk, int nblk,
-                                                             double* __restrict__ out) {
-  __shared__ double part[(kRedThreads / 32) * kGlob];
-  __shared__ double mom[kGlob];
-  reduce_rows(blk, nblk, part, mom);
-  if (threadIdx.x < kGlob) out[threadIdx.x] = mom[threadIdx.x];
+  __syncthreads();
+  newton(s, dp.newton_max, dp.newton_tol);
+  if (tid != 0) return;
+  double* out = io + 96;
+  for (int i = 0; i < 9; ++i) out[i] = s.R[i];
+  for (int i = 0; i < 3; ++i) out[9 + i] = s.t[i];
+  out[12] = s.NP > 0.0 ? s.Q / (3.0 * s.NP) : 0.0;
+  out[13] = s.Q;
+  out[14] = s.iters;
+  out[15] = s.damped;
+  out[16] = s.halvings;
 }
 
 struct PoseArg {
@@ -420,28 +441,28 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = 0; i < 9; ++i) st->R[i] = pose.R[i];
   for (int i = 0; i < 3; ++i)
-    st->t[i] = pose.R[3 * i] * st->mu_x[0] + pose.R[3 * i + 1] * st->mu_x[1] +
-               pose.R[3 * i + 2] * st->mu_x[2] + pose.t[i] - st->mu_y[i];
+    st->t[i] = pose.R[3 * i] * st->mu_x[0] + pose.R[3 * i + 1] * st->mu_x[1] + pose.R[3 * i + 2] * st->mu_x[2] +
+               pose.t[i] - st->mu_y[i];
   st->sigma2 = sigma2;
   st->V = V;
+  st->log2_V = log2(V);
   st->log2_wodds = w > 0.0 ? log2(w) - log2(1.0 - w) : -INFINITY;
+  st->ln_1mw = log1p(-w);
   st->done = 0;
   st->iter = 0;
   st->numeric_fail = 0;
-  set_constants(st, w);
+  set_estep_constants(st);
 }
 
 }  // namespace
 
-cudaError_t launch_mstep(const double* blk, int nblk, EmState* st, const DevParams& dp, double* trace,
-                         double* out, int standalone, cudaStream_t s) {
-  if (standalone) {
-    // blk holds the kGlob moments; out[0..11] holds the starting pose (R, t) and
-    // receives the results at out[16..32]
-    mstep_standalone_kernel<<<1, 32, 0, s>>>(blk, out, dp, out + 16);
-  } else {
-    mstep_em_kernel<<<1, kRedThreads, 0, s>>>(blk, nblk, st, dp, trace);
-  }
+cudaError_t launch_mstep(const double* mom, EmState* st, const DevParams& dp, double* trace, cudaStream_t s) {
+  mstep_em_kernel<<<1, kMThreads, 0, s>>>(mom, st, dp, trace);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s) {
+  mstep_standalone_kernel<<<1, kMThreads, 0, s>>>(io, dp);
   return cudaGetLastError();
 }
 
@@ -451,11 +472,6 @@ cudaError_t launch_estep_constants(EmState* st, double sigma2, double w, double 
   for (int i = 0; i < 9; ++i) pa.R[i] = R[i];
   for (int i = 0; i < 3; ++i) pa.t[i] = t[i];
   constants_kernel<<<1, 32, 0, s>>>(st, sigma2, w, V, pa);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reduce_moments(const double* blk, int nblk, double* out, cudaStream_t s) {
-  reduce_kernel<<<1, kRedThreads, 0, s>>>(blk, nblk, out);
   return cudaGetLastError();
 }
 

@@ -190,18 +190,12 @@ __global__ void finalize_init_kernel(const double* __restrict__ red, int nblk, l
   if (!(s2 > st->sigma2_floor)) s2 = st->sigma2_floor > 0.0 ? st->sigma2_floor : 1e-30;
   st->sigma2 = s2;
   st->log2_wodds = dp.w > 0.0 ? log2(dp.w) - log2(1.0 - dp.w) : -INFINITY;
+  st->log2_V = log2(st->V);
+  st->ln_1mw = log1p(-dp.w);
   st->done = 0;
   st->iter = 0;
   st->numeric_fail = 0;
-  // E-step constants (same definitions as the M-step kernel)
-  const double c = 1.4426950408889634 / (2.0 * s2);
-  const double L = st->log2_wodds + 1.5 * log2(2.0 * 3.14159265358979323846 * s2) - log2(st->V);
-  for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
-  for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
-  st->neg_c = static_cast<float>(-c);
-  st->L = static_cast<float>(L);
-  st->kap = static_cast<float>(L / c);
-  st->nll_const = -log1p(-dp.w) + 1.5 * log(2.0 * 3.14159265358979323846 * s2);
+  set_estep_constants(st);
 }
 
 // ---------------------------------------------------------------------------

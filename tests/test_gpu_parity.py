@@ -117,7 +117,8 @@ def test_mstep_matches_oracle_newton(ctx):
     assert oracle.rotation_error(got["R"], ref["R"]) < 1e-9
     np.testing.assert_allclose(got["t"], ref["t"], atol=1e-9)
     assert got["sigma2"] == pytest.approx(ref["sigma2"], rel=1e-9)
-    assert got["newton_iters"] == ref["newton_iters"]
+    # the Newton direction is solved in FP32 (FP64 residual): the path may take one more step
+    assert abs(got["newton_iters"] - ref["newton_iters"]) <= 1
 
 
 @pytest.mark.parametrize("which", ["sphere_plane", "random", "rgbd_full"])
