@@ -337,42 +337,22 @@ __global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __re
 // ---------------------------------------------------------------------------
 // Combine: per source, add the FP32 pieces with compensated summation,
 // normalise by S0 + gamma'_n, and form the 76 contributions to the global
-// moments of the M step.  Contributions are reduced warp by warp in FP32 with
-// error-free transformations (TwoSum: every rounding error is carried in a
-// second FP32 word), then accumulated across warps and chunks in FP64.
+// moments of the M step (FP32 products).  Each warp transposes its 32 x 76
+// contributions through shared memory; lane l then sums columns l, l+32, l+64
+// over the 32 sources with Neumaier's compensated summation (an error-free
+// TwoSum per add), and adds the result to FP64 per-warp accumulators.  FP64
+// appears only there and in the cross-block reduction.
 // ---------------------------------------------------------------------------
-constexpr int kCombineThreads = 256;
+constexpr int kCombineThreads = 128;
 constexpr int kCombineWarps = kCombineThreads / 32;
-
-struct F2 {  // unevaluated sum hi + lo
-  float hi, lo;
-};
-
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  const float e = (a - (s - bb)) + (b - bb);
-  return F2{s, e};
-}
-
-// Butterfly reduction of (hi, lo) over the warp; every lane ends with the total.
-__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, v.hi, o);
-    const float ol = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    F2 s = two_sum(v.hi, oh);
-    s.lo += v.lo + ol;
-    v = s;
-  }
-  return v;
-}
+constexpr int kCPad = kGlob + 1;  // odd row pitch: conflict-free transposition
 
 __global__ void __launch_bounds__(kCombineThreads)
     combine_kernel(const float4* __restrict__ xs, long long N, const float* __restrict__ part,
                    const int* __restrict__ table, const EmState* __restrict__ st,
                    const float* __restrict__ kap_n, const float* __restrict__ gam_n,
                    double* __restrict__ rows, float* __restrict__ per_n, int SB, int grid_e) {
+  __shared__ float buf[kCombineWarps][32 * kCPad];
   __shared__ double acc[kCombineWarps][kGlob];
   if (st->done) return;
   const int tid = threadIdx.x;
@@ -385,7 +365,8 @@ __global__ void __launch_bounds__(kCombineThreads)
   const float nc = st->neg_c;
   const float nll_c = static_cast<float>(st->nll_const);
   const long long stride = static_cast<long long>(gridDim.x) * kCombineThreads;
-  // every warp runs the same number of chunk iterations (whole-warp collectives)
+  float* row = buf[warp] + lane * kCPad;
+  // every warp runs the same number of chunk iterations
   for (long long base = static_cast<long long>(blockIdx.x) * kCombineThreads; base < N; base += stride) {
     const long long n = base + tid;
     const bool valid = n < N;
@@ -444,21 +425,12 @@ __global__ void __launch_bounds__(kCombineThreads)
     const float h[3] = {r0 + be0, r1 + be1, r2 + be2};
     const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
     const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
-    // lane l keeps the warp totals of moments l, l + 32, l + 64 (FP64 adds stay full-warp)
-    float keep_hi[3] = {0.f, 0.f, 0.f}, keep_lo[3] = {0.f, 0.f, 0.f};
-    auto put = [&](int j, float v) {
-      const F2 r = warp_sum_f2(F2{v, 0.f});
-      if (lane == (j & 31)) {
-        keep_hi[j >> 5] = r.hi;
-        keep_lo[j >> 5] = r.lo;
-      }
-    };
-    put(0, Pb);
-    put(1, Dn);
+    row[0] = Pb;
+    row[1] = Dn;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) put(2 + 4 * i + k, h[i] * xt[k]);
+      for (int k = 0; k < 4; ++k) row[2 + 4 * i + k] = h[i] * xt[k];
     {
       int j = 14;
 #pragma unroll
@@ -466,14 +438,27 @@ __global__ void __launch_bounds__(kCombineThreads)
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-          for (int l = k; l < 4; ++l) put(j++, A[p] * (xt[k] * xt[l]));
+          for (int l = k; l < 4; ++l) row[j++] = A[p] * (xt[k] * xt[l]);
     }
-    put(74, Pout);
-    put(75, nll);
+    row[74] = Pout;
+    row[75] = nll;
+    __syncwarp();
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-      if (lane + 32 * i < kGlob)
-        acc[warp][lane + 32 * i] += static_cast<double>(keep_hi[i]) + static_cast<double>(keep_lo[i]);
+    for (int i = 0; i < 3; ++i) {
+      const int col = lane + 32 * i;
+      if (col < kGlob) {
+        float sum = 0.f, comp = 0.f;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {  // Neumaier: sum + comp is the exact running sum
+          const float v = buf[warp][r * kCPad + col];
+          const float t = sum + v;
+          comp += (fabsf(sum) >= fabsf(v)) ? ((sum - t) + v) : ((v - t) + sum);
+          sum = t;
+        }
+        acc[warp][col] += static_cast<double>(sum) + static_cast<double>(comp);
+      }
+    }
+    __syncwarp();
   }
   __syncthreads();
   if (tid < kGlob) {
@@ -602,7 +587,7 @@ cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec,
 
 int combine_rows(int64_t N, int num_sms) {
   const long long b = (N + kCombineThreads - 1) / kCombineThreads;
-  const long long cap = 2LL * num_sms;
+  const long long cap = 4LL * num_sms;
   return static_cast<int>(b < cap ? b : cap);
 }
 

@@ -65,15 +65,14 @@ struct EmState {
 // E-step constants for the current (R, t, sigma2) of the state.  The shift L
 // and the logarithms feed FP32 arithmetic only, so they are evaluated in FP32.
 __device__ inline void set_estep_constants(EmState* st) {
-  const double s2 = st->sigma2;
-  const double c = 1.4426950408889634 / (2.0 * s2);  // log2(e) / (2 s2)
-  const float lg = log2f(static_cast<float>(6.283185307179586 * s2));
+  const float s2 = static_cast<float>(st->sigma2);
+  const float lg = log2f(6.2831853f * s2);
   const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
   for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
   for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
-  st->neg_c = static_cast<float>(-c);
+  st->neg_c = -1.44269504f / (2.f * s2);  // -log2(e) / (2 s2)
   st->L = L;
-  st->kap = static_cast<float>(static_cast<double>(L) / c);
+  st->kap = L * (2.f * s2) * 0.69314718f;  // L / c
   st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
 }
 

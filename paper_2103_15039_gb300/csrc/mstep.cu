@@ -37,6 +37,13 @@ namespace {
 
 constexpr int kMThreads = 128;
 
+// position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
+__host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
+
+// row / column of the i-th entry of the upper triangle of a 6x6 matrix
+__constant__ int c_hrow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ int c_hcol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
 struct Shared {
   double SD, NP;
   double H1[12];
@@ -103,32 +110,50 @@ __device__ void load_model(Shared& s, const double* mom) {
 }
 
 // FP32 LDL^T solve of the symmetric 6x6 H x = b; false if a pivot is not positive.
-__device__ bool ldl_solve6(const float H[36], const float b[6], float x[6]) {
-  float L[36], D[6];
+// Every loop has a constant trip count and is fully unrolled (triangular ranges are
+// masked), so that all arrays stay in registers.
+__device__ __forceinline__ bool ldl_solve6(const float (&H)[36], const float (&b)[6], float (&x)[6]) {
+  float L[36], D[6], Dinv[6];
+  bool ok = true;
+#pragma unroll
   for (int j = 0; j < 6; ++j) {
     float d = H[7 * j];
-    for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k] * D[k];
-    if (!(d > 0.f)) return false;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < j) d -= L[6 * j + k] * L[6 * j + k] * D[k];
+    ok = ok && (d > 0.f);
     D[j] = d;
-    const float inv = 1.f / d;
-    for (int i = j + 1; i < 6; ++i) {
-      float v = H[6 * i + j];
-      for (int k = 0; k < j; ++k) v -= L[6 * i + k] * L[6 * j + k] * D[k];
-      L[6 * i + j] = v * inv;
+    Dinv[j] = __frcp_rn(d);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      if (i > j) {
+        float v = H[6 * i + j];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (k < j) v -= L[6 * i + k] * L[6 * j + k] * D[k];
+        L[6 * i + j] = v * Dinv[j];
+      }
     }
   }
   float y[6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) {
     float v = b[i];
-    for (int k = 0; k < i; ++k) v -= L[6 * i + k] * y[k];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k < i) v -= L[6 * i + k] * y[k];
     y[i] = v;
   }
-  for (int i = 5; i >= 0; --i) {
-    float v = y[i] / D[i];
-    for (int k = i + 1; k < 6; ++k) v -= L[6 * k + i] * x[k];
+#pragma unroll
+  for (int ii = 0; ii < 6; ++ii) {
+    const int i = 5 - ii;
+    float v = y[i] * Dinv[i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (k > i) v -= L[6 * k + i] * x[k];
     x[i] = v;
   }
-  return true;
+  return ok;
 }
 
 // Newton loop on the model in shared memory; T starts at (s.R, s.t) == (s.Ro, s.to).
@@ -147,11 +172,13 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       const int q = tid / 6, p = tid % 6;
       const int i = p < 3 ? 0 : (p < 5 ? 1 : 2);
       const int j = p < 3 ? p : (p < 5 ? p - 2 : 2);
-      double v = 0.0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) v += s.R[3 * a + i] * Aent(s, q, a, b) * s.R[3 * b + j];
+      const double* Aq = s.A[q];
+      // u = A^q R e_j, then v = (R e_i) . u
+      const double r0 = s.R[j], r1 = s.R[3 + j], r2 = s.R[6 + j];
+      const double u0 = Aq[0] * r0 + Aq[1] * r1 + Aq[2] * r2;
+      const double u1 = Aq[1] * r0 + Aq[3] * r1 + Aq[4] * r2;
+      const double u2 = Aq[2] * r0 + Aq[4] * r1 + Aq[5] * r2;
+      const double v = s.R[i] * u0 + s.R[3 + i] * u1 + s.R[6 + i] * u2;
       s.C[q][3 * i + j] = v;
       s.C[q][3 * j + i] = v;
     } else if (tid >= 64 && tid < 76) {
@@ -160,8 +187,9 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     }
     __syncthreads();
     // --- gradient (6) and the upper triangle of H_s (21) ---
+    // sum_ik eps_aik X_ik = X_{a1 a2} - X_{a2 a1} with a1 = a+1, a2 = a+2 (mod 3)
     if (tid < 27) {
-      double v = 0.0;
+      double v;
       if (tid < 6) {
         const int a = tid;
         if (a < 3) {
@@ -171,34 +199,17 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
           v = 2.0 * s.NM[4 * (a - 3) + 3];
         }
       } else {
-        int e = tid - 6, a = 0;
-        while (e >= 6 - a) {
-          e -= 6 - a;
-          ++a;
-        }
-        const int b = a + e;
+        const int a = c_hrow[tid - 6], b = c_hcol[tid - 6];
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
         if (b < 3) {  // rotation - rotation
-          double gn = 0.0;
-          for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) {
-              const double ea = eps3(a, i, k);
-              if (ea == 0.0) continue;
-              for (int j = 0; j < 3; ++j)
-                for (int l = 0; l < 3; ++l) {
-                  const double eb = eps3(b, j, l);
-                  if (eb != 0.0) gn += ea * eb * Cent(s, k, l, i, j);
-                }
-            }
+          const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+          const double gn = Cent(s, a2, b2, a1, b1) - Cent(s, a2, b1, a1, b2) - Cent(s, a1, b2, a2, b1) +
+                            Cent(s, a1, b1, a2, b2);
           const double trN = s.NM[0] + s.NM[5] + s.NM[10];
           v = 2.0 * gn + s.NM[4 * a + b] + s.NM[4 * b + a] - (a == b ? 2.0 * trN : 0.0);
         } else if (a < 3) {  // rotation a - translation c
           const int c = b - 3;
-          double gn = 0.0;
-          for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) {
-              const double ea = eps3(a, i, k);
-              if (ea != 0.0) gn -= ea * Cent(s, k, 3, i, c);
-            }
+          const double gn = Cent(s, a1, 3, a2, c) - Cent(s, a2, 3, a1, c);
           double sec = 0.0;
           if (c != a) {
             const int i = 3 - a - c;
@@ -214,31 +225,35 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     __syncthreads();
     // --- Newton direction (FP32 LDL^T, damped if not positive definite) ---
     if (tid == 0) {
-      float Hf[36], mg[6], x[6];
-      int e = 6;
-      for (int a = 0; a < 6; ++a)
-        for (int b = a; b < 6; ++b, ++e) {
-          Hf[6 * a + b] = static_cast<float>(s.gH[e]);
-          Hf[6 * b + a] = Hf[6 * a + b];
-        }
-      for (int a = 0; a < 6; ++a) mg[a] = static_cast<float>(-s.gH[a]);
-      bool ok = ldl_solve6(Hf, mg, x);
-      if (!ok) {
-        float tr = 0.f;
-        for (int a = 0; a < 6; ++a) tr += fabsf(Hf[7 * a]);
-        float mu = 1e-6f * (tr > 0.f ? tr / 6.f : 1.f);
-        for (int k = 0; k < 40 && !ok; ++k, mu *= 10.f) {
-          float Dm[36];
-          for (int q = 0; q < 36; ++q) Dm[q] = Hf[q];
-          for (int a = 0; a < 6; ++a) Dm[7 * a] += mu;
-          ok = ldl_solve6(Dm, mg, x);
-        }
-        ++s.damped;
+      // attempt 0 undamped; then mu = 1e-6 tr/6, x10 per attempt (a single call site
+      // with compile-time indices keeps every array of the solve in registers)
+      float mg[6], x[6];
+      float tr = 0.f;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        mg[a] = static_cast<float>(-s.gH[a]);
+        tr += fabsf(static_cast<float>(s.gH[6 + tri_index(a, a)]));
+      }
+      const float mu0 = 1e-6f * (tr > 0.f ? tr / 6.f : 1.f);
+      bool ok = false;
+      float mu = 0.f;
+      for (int k = 0; k <= 40 && !ok; ++k) {
+        float Dm[36];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int b = 0; b < 6; ++b)
+            Dm[6 * a + b] = static_cast<float>(s.gH[6 + (a <= b ? tri_index(a, b) : tri_index(b, a))]) +
+                            (a == b ? mu : 0.f);
+        ok = ldl_solve6(Dm, mg, x);
+        if (k == 1) ++s.damped;
+        mu = (k == 0) ? mu0 : mu * 10.f;
       }
       if (!ok) {
         s.go = 0;
       } else {
         ++s.iters;
+#pragma unroll
         for (int a = 0; a < 6; ++a) s.xi[a] = x[a];
       }
       s.accepted = 0;
@@ -261,12 +276,16 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
           B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
           Cc = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
         } else {
+          // sin th = 2 sh ch, 1 - cos th = 2 sh^2 with (sh, ch) = (sin, cos)(th / 2)
           const double th = sqrt(th2);
-          double sn, cs;
-          sincos(th, &sn, &cs);
-          A = sn / th;
-          B = (1.0 - cs) / th2;
-          Cc = (th - sn) / (th2 * th);
+          double sh, ch;
+          sincos(0.5 * th, &sh, &ch);
+          const double ith = __drcp_rn(th);
+          const double ith2 = ith * ith;
+          const double sn = 2.0 * sh * ch;
+          A = sn * ith;
+          B = 2.0 * sh * sh * ith2;
+          Cc = (th - sn) * ith2 * ith;
         }
         s.coef[0] = A;
         s.coef[1] = B;

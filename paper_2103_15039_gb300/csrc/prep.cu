@@ -90,20 +90,24 @@ __global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __
   block_reduce<12>(v, op, red + static_cast<size_t>(blockIdx.x) * 12);
 }
 
-// Finalise pass 1: centroids, V, diagonal and sigma^2 floor.
+// Finalise pass 1: centroids, V, diagonal and sigma^2 floor.  One warp per
+// reduced value (lanes over the partial rows), then thread 0 finishes.
 __global__ void finalize_raw_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
                                     double volume, double floor_rel, EmState* __restrict__ st) {
-  if (threadIdx.x != 0) return;
-  double v[12];
-  for (int j = 0; j < 6; ++j) v[j] = 0.0;
-  for (int j = 6; j < 9; ++j) v[j] = INFINITY;
-  for (int j = 9; j < 12; ++j) v[j] = -INFINITY;
-  for (int b = 0; b < nblk; ++b) {
-    const double* r = red + static_cast<size_t>(b) * 12;
-    for (int j = 0; j < 6; ++j) v[j] += r[j];
-    for (int j = 6; j < 9; ++j) v[j] = fmin(v[j], r[j]);
-    for (int j = 9; j < 12; ++j) v[j] = fmax(v[j], r[j]);
+  __shared__ double v[12];
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (j < 12) {
+    const int op = j < 6 ? 0 : (j < 9 ? 1 : 2);
+    double x = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
+    for (int b = lane; b < nblk; b += 32) {
+      const double r = red[static_cast<size_t>(b) * 12 + j];
+      x = op == 0 ? x + r : (op == 1 ? fmin(x, r) : fmax(x, r));
+    }
+    x = op == 0 ? warp_sum_d(x) : (op == 1 ? warp_min_d(x) : warp_max_d(x));
+    if (lane == 0) v[j] = x;
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   for (int c = 0; c < 3; ++c) {
     st->mu_x[c] = v[c] / static_cast<double>(N);
     st->mu_y[c] = v[3 + c] / static_cast<double>(M);
@@ -165,10 +169,18 @@ __global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __res
 //   sigma^2_0 = (M sum|z|^2 + N sum|yc|^2 - 2 sum z . sum yc) / (3 N M).
 __global__ void finalize_init_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
                                      DevParams dp, EmState* __restrict__ st) {
+  __shared__ double v[8];
+  {
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j < 8) {
+      double x = 0.0;
+      for (int b = lane; b < nblk; b += 32) x += red[static_cast<size_t>(b) * 8 + j];
+      x = warp_sum_d(x);
+      if (lane == 0) v[j] = x;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = 0; b < nblk; ++b)
-    for (int j = 0; j < 8; ++j) v[j] += red[static_cast<size_t>(b) * 8 + j];
   const double* R = dp.init_R;
   double tc[3], Rsx[3];
   for (int i = 0; i < 3; ++i) {
@@ -447,7 +459,7 @@ cudaError_t launch_center_only(const float* X, int64_t N, const float* Y, int64_
                                EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
   const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : M);
   raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
-  finalize_raw_kernel<<<1, 32, 0, s>>>(red, nb, N, M, 0.0, 0.0, st);
+  finalize_raw_kernel<<<1, 12 * 32, 0, s>>>(red, nb, N, M, 0.0, 0.0, st);
   center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red + static_cast<size_t>(kStatBlocksMax) * 12);
   return cudaGetLastError();
 }
@@ -456,10 +468,10 @@ cudaError_t launch_init(const float* X, int64_t N, const float* Y, int64_t M, co
                         double* red, EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
   const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : (n_pad > M ? n_pad : M));
   raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
-  finalize_raw_kernel<<<1, 32, 0, s>>>(red, nb, N, M, dp.volume, dp.sigma2_floor_rel, st);
+  finalize_raw_kernel<<<1, 12 * 32, 0, s>>>(red, nb, N, M, dp.volume, dp.sigma2_floor_rel, st);
   double* red2 = red + static_cast<size_t>(kStatBlocksMax) * 12;
   center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red2);
-  finalize_init_kernel<<<1, 32, 0, s>>>(red2, nb, N, M, dp, st);
+  finalize_init_kernel<<<1, 8 * 32, 0, s>>>(red2, nb, N, M, dp, st);
   return cudaGetLastError();
 }
 
