@@ -37,6 +37,14 @@ namespace {
 
 constexpr int kMThreads = 128;
 
+// Power-series coefficients (-1)^k / (2k + o)! of sin(th)/th (o = 1), (1 - cos th)/th^2
+// (o = 2) and (th - sin th)/th^3 (o = 3) in powers of th^2, k = 0..8; the truncation
+// error is below 1e-19 for th^2 <= 1/4.
+__constant__ double c_exp_series[3][9] = {
+    {1.0, -0.16666666666666666, 0.008333333333333333, -0.0001984126984126984, 2.7557319223985893e-06, -2.505210838544172e-08, 1.6059043836821613e-10, -7.647163731819816e-13, 2.8114572543455206e-15},
+    {0.5, -0.041666666666666664, 0.001388888888888889, -2.48015873015873e-05, 2.755731922398589e-07, -2.08767569878681e-09, 1.1470745597729725e-11, -4.779477332387385e-14, 1.5619206968586225e-16},
+    {0.16666666666666666, -0.008333333333333333, 0.0001984126984126984, -2.7557319223985893e-06, 2.505210838544172e-08, -1.6059043836821613e-10, 7.647163731819816e-13, -2.8114572543455206e-15, 8.22063524662433e-18}};
+
 // position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
 
@@ -55,6 +63,8 @@ struct Shared {
   double C[10][9];
   double NM[12];
   double gH[27];   // grad (6) then the upper triangle of H_s (21)
+  float gHf[27];   // the same in FP32 for the direction solve
+  float xf[6];     // Newton direction (FP32)
   double xi[6];
   double coef[3];  // exp coefficients
   double wv[6];    // scaled step
@@ -221,6 +231,7 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         }
       }
       s.gH[tid] = v;
+      s.gHf[tid] = static_cast<float>(v);
     }
     __syncthreads();
     // --- Newton direction (FP32 LDL^T, damped if not positive definite) ---
@@ -231,8 +242,8 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       float tr = 0.f;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        mg[a] = static_cast<float>(-s.gH[a]);
-        tr += fabsf(static_cast<float>(s.gH[6 + tri_index(a, a)]));
+        mg[a] = -s.gHf[a];
+        tr += fabsf(s.gHf[6 + tri_index(a, a)]);
       }
       const float mu0 = 1e-6f * (tr > 0.f ? tr / 6.f : 1.f);
       bool ok = false;
@@ -243,8 +254,7 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         for (int a = 0; a < 6; ++a)
 #pragma unroll
           for (int b = 0; b < 6; ++b)
-            Dm[6 * a + b] = static_cast<float>(s.gH[6 + (a <= b ? tri_index(a, b) : tri_index(b, a))]) +
-                            (a == b ? mu : 0.f);
+            Dm[6 * a + b] = s.gHf[6 + (a <= b ? tri_index(a, b) : tri_index(b, a))] + (a == b ? mu : 0.f);
         ok = ldl_solve6(Dm, mg, x);
         if (k == 1) ++s.damped;
         mu = (k == 0) ? mu0 : mu * 10.f;
@@ -254,7 +264,7 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       } else {
         ++s.iters;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) s.xi[a] = x[a];
+        for (int a = 0; a < 6; ++a) s.xf[a] = x[a];
       }
       s.accepted = 0;
     }
@@ -263,37 +273,28 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     // --- backtracking on the exact FP64 change of Q_d ---
     double step = 1.0;
     for (int bt = 0; bt <= 10; ++bt, step *= 0.5) {
-      if (tid == 0) {
-        double w[3], v[3];
-        for (int a = 0; a < 3; ++a) {
-          w[a] = step * s.xi[a];
-          v[a] = step * s.xi[3 + a];
-        }
-        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        double A, B, Cc;  // sin(th)/th, (1 - cos th)/th^2, (th - sin th)/th^3
-        if (th2 < 1e-8) {
-          A = 1.0 - th2 / 6.0 + th2 * th2 / 120.0;
-          B = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-          Cc = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
+      if (tid < 6) s.wv[tid] = step * static_cast<double>(s.xf[tid]);
+      __syncthreads();
+      if (tid < 3) {
+        // exp coefficients A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3 as
+        // power series in th^2 (Horner, converged to FP64 for th <= 0.5), else from sincos
+        const double* w = s.wv;
+        const double x = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        double cf;
+        if (x <= 0.25) {
+          const double* c = c_exp_series[tid];
+          double r = c[8];
+#pragma unroll
+          for (int k = 7; k >= 0; --k) r = fma(r, x, c[k]);
+          cf = r;
         } else {
-          // sin th = 2 sh ch, 1 - cos th = 2 sh^2 with (sh, ch) = (sin, cos)(th / 2)
-          const double th = sqrt(th2);
+          const double th = sqrt(x);
           double sh, ch;
           sincos(0.5 * th, &sh, &ch);
-          const double ith = __drcp_rn(th);
-          const double ith2 = ith * ith;
           const double sn = 2.0 * sh * ch;
-          A = sn * ith;
-          B = 2.0 * sh * sh * ith2;
-          Cc = (th - sn) * ith2 * ith;
+          cf = tid == 0 ? sn / th : (tid == 1 ? 2.0 * sh * sh / x : (th - sn) / (x * th));
         }
-        s.coef[0] = A;
-        s.coef[1] = B;
-        s.coef[2] = Cc;
-        for (int a = 0; a < 3; ++a) {
-          s.wv[a] = w[a];
-          s.wv[3 + a] = v[a];
-        }
+        s.coef[tid] = cf;
       }
       __syncthreads();
       // E = I + A W + B W^2 and V v = v + B W v + C W^2 v with W = [w]x, W^2 = w w^T - th^2 I
@@ -394,26 +395,45 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     return;
   }
   newton(s, dp.newton_max, dp.newton_tol);
-  if (tid != 0) return;
-  // motion of this iteration in the caller's frame (diagnostic, FP32 angle)
-  double fro = 0.0, dtr2 = 0.0;
-  for (int i = 0; i < 9; ++i) fro += (s.R[i] - s.Ro[i]) * (s.R[i] - s.Ro[i]);
-  for (int i = 0; i < 3; ++i) {
+  // --- epilogue, lane-parallel: state, E-step constants, diagnostics ---
+  __shared__ float dmot[12];
+  __shared__ double s2_sh;
+  __shared__ int done_sh;
+  if (tid < 9) {
+    dmot[tid] = static_cast<float>(s.R[tid] - s.Ro[tid]);
+  } else if (tid < 12) {
+    const int i = tid - 9;
     double d = s.t[i] - s.to[i];
     for (int j = 0; j < 3; ++j) d -= (s.R[3 * i + j] - s.Ro[3 * i + j]) * st->mu_x[j];
-    dtr2 += d * d;
+    dmot[tid] = static_cast<float>(d);
+  } else if (tid == 32) {
+    const double s2 = s.Q * __drcp_rn(3.0 * s.NP);
+    const bool at_floor = !(s2 > st->sigma2_floor);
+    s2_sh = at_floor ? st->sigma2_floor : s2;
+    const int it = st->iter;
+    done_sh = at_floor || it + 1 >= dp.max_iters;
   }
-  const float ang = 2.f * asinf(fminf(1.f, sqrtf(static_cast<float>(fro)) * 0.35355339f));
-  const float motion = fmaxf(ang, sqrtf(static_cast<float>(dtr2)) / static_cast<float>(st->diag > 0 ? st->diag : 1.0));
-  const double s2 = s.Q / (3.0 * s.NP);
-  const bool at_floor = !(s2 > st->sigma2_floor);
-  for (int i = 0; i < 9; ++i) st->R[i] = s.R[i];
-  for (int i = 0; i < 3; ++i) st->t[i] = s.t[i];
-  st->sigma2 = at_floor ? st->sigma2_floor : s2;
+  __syncthreads();
+  // new pose (FP64) and its FP32 copies for the next E step
+  if (tid < 9) {
+    st->R[tid] = s.R[tid];
+    st->Rf[tid] = static_cast<float>(s.R[tid]);
+  } else if (tid < 12) {
+    st->t[tid - 9] = s.t[tid - 9];
+    st->tf[tid - 9] = static_cast<float>(s.t[tid - 9]);
+  }
+  if (tid != 0) return;
+  float fro = 0.f;
+  for (int i = 0; i < 9; ++i) fro += dmot[i] * dmot[i];
+  const float ang = 2.f * asinf(fminf(1.f, sqrtf(fro) * 0.35355339f));
+  const float dtr = sqrtf(dmot[9] * dmot[9] + dmot[10] * dmot[10] + dmot[11] * dmot[11]);
+  const float motion = fmaxf(ang, dtr / static_cast<float>(st->diag > 0 ? st->diag : 1.0));
+  const double s2 = s2_sh;
+  st->sigma2 = s2;
   const int it = st->iter;
   if (trace) {
     double* tr = trace + static_cast<size_t>(it) * 8;
-    tr[0] = st->sigma2;
+    tr[0] = s2;
     tr[1] = s.NP;
     tr[2] = s.Q;
     tr[3] = s.iters;
@@ -423,8 +443,15 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     tr[7] = mom[74];
   }
   st->iter = it + 1;
-  if (at_floor || (dp.tol > 0.0 && motion < dp.tol) || st->iter >= dp.max_iters) st->done = 1;
-  set_estep_constants(st);
+  if (done_sh || (dp.tol > 0.0 && motion < dp.tol)) st->done = 1;
+  // E-step constants (the rotation/translation copies were written above)
+  const float s2f = static_cast<float>(s2);
+  const float lg = log2f(6.2831853f * s2f);
+  const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
+  st->neg_c = -1.44269504f / (2.f * s2f);
+  st->L = L;
+  st->kap = L * (2.f * s2f) * 0.69314718f;
+  st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
 }
 
 __global__ void __launch_bounds__(kMThreads) mstep_standalone_kernel(double* __restrict__ io, DevParams dp) {
