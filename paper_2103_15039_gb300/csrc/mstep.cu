@@ -45,6 +45,95 @@ __constant__ double c_exp_series[3][9] = {
     {0.5, -0.041666666666666664, 0.001388888888888889, -2.48015873015873e-05, 2.755731922398589e-07, -2.08767569878681e-09, 1.1470745597729725e-11, -4.779477332387385e-14, 1.5619206968586225e-16},
     {0.16666666666666666, -0.008333333333333333, 0.0001984126984126984, -2.7557319223985893e-06, 2.505210838544172e-08, -1.6059043836821613e-10, 7.647163731819816e-13, -2.8114572543455206e-15, 8.22063524662433e-18}};
 
+// Gradient and symmetrised Hessian entries as fixed linear combinations of the
+// entries of C (10 pairs x 9) and of NM = R^T M1 (3 x 4):
+//   entry e = sum_t cc[e][t] * C_flat[ic[e][t]] + sum_t cn[e][t] * NM[in[e][t]]
+// e = 0..5: gradient; e = 6..26: upper triangle of H_s in row-major order.
+// Built at compile time from the closed forms in the file comment.
+struct HessTab {
+  int ic[27][4];
+  double cc[27][4];
+  int in[27][3];
+  double cn[27][3];
+};
+
+__host__ __device__ constexpr int pair_q_c(int k, int l) {
+  return k > l ? pair_q_c(l, k) : (k == 0 ? l : (k == 1 ? 3 + l : (k == 2 ? 5 + l : 9)));
+}
+__host__ __device__ constexpr int cflat(int k, int l, int i, int j) { return pair_q_c(k, l) * 9 + 3 * i + j; }
+__host__ __device__ constexpr double eps_c(int a, int b, int c) {
+  return (a == b || b == c || a == c) ? 0.0 : (((b - a + 3) % 3 == 1) ? 1.0 : -1.0);
+}
+
+__host__ __device__ constexpr HessTab make_hess_tab() {
+  HessTab h{};
+  for (int e = 0; e < 27; ++e)
+    for (int t = 0; t < 4; ++t) {
+      h.ic[e][t] = 0;
+      h.cc[e][t] = 0.0;
+      if (t < 3) {
+        h.in[e][t] = 0;
+        h.cn[e][t] = 0.0;
+      }
+    }
+  for (int a = 0; a < 6; ++a) {  // gradient
+    if (a < 3) {
+      const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+      h.in[a][0] = 4 * a2 + a1;
+      h.cn[a][0] = 2.0;
+      h.in[a][1] = 4 * a1 + a2;
+      h.cn[a][1] = -2.0;
+    } else {
+      h.in[a][0] = 4 * (a - 3) + 3;
+      h.cn[a][0] = 2.0;
+    }
+  }
+  int e = 6;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b, ++e) {
+      const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+      if (b < 3) {
+        const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+        h.ic[e][0] = cflat(a2, b2, a1, b1);
+        h.cc[e][0] = 2.0;
+        h.ic[e][1] = cflat(a2, b1, a1, b2);
+        h.cc[e][1] = -2.0;
+        h.ic[e][2] = cflat(a1, b2, a2, b1);
+        h.cc[e][2] = -2.0;
+        h.ic[e][3] = cflat(a1, b1, a2, b2);
+        h.cc[e][3] = 2.0;
+        if (a != b) {  // N_ab + N_ba
+          h.in[e][0] = 4 * a + b;
+          h.cn[e][0] = 1.0;
+          h.in[e][1] = 4 * b + a;
+          h.cn[e][1] = 1.0;
+        } else {  // 2 N_aa - 2 tr N
+          for (int i = 0; i < 3; ++i) {
+            h.in[e][i] = 5 * i;
+            h.cn[e][i] = (i == a) ? 0.0 : -2.0;
+          }
+        }
+      } else if (a < 3) {
+        const int c = b - 3;
+        h.ic[e][0] = cflat(a1, 3, a2, c);
+        h.cc[e][0] = 2.0;
+        h.ic[e][1] = cflat(a2, 3, a1, c);
+        h.cc[e][1] = -2.0;
+        if (c != a) {
+          const int i = 3 - a - c;
+          h.in[e][0] = 4 * i + 3;
+          h.cn[e][0] = eps_c(a, c, i);
+        }
+      } else {
+        h.ic[e][0] = cflat(3, 3, a - 3, b - 3);
+        h.cc[e][0] = 2.0;
+      }
+    }
+  return h;
+}
+
+__constant__ HessTab c_hess = make_hess_tab();
+
 // position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
 
@@ -196,40 +285,14 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       s.NM[e] = s.R[i] * s.M1[k] + s.R[3 + i] * s.M1[4 + k] + s.R[6 + i] * s.M1[8 + k];
     }
     __syncthreads();
-    // --- gradient (6) and the upper triangle of H_s (21) ---
-    // sum_ik eps_aik X_ik = X_{a1 a2} - X_{a2 a1} with a1 = a+1, a2 = a+2 (mod 3)
+    // --- gradient (6) and the upper triangle of H_s (21): branch-free table form ---
     if (tid < 27) {
-      double v;
-      if (tid < 6) {
-        const int a = tid;
-        if (a < 3) {
-          const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-          v = 2.0 * (s.NM[4 * a2 + a1] - s.NM[4 * a1 + a2]);
-        } else {
-          v = 2.0 * s.NM[4 * (a - 3) + 3];
-        }
-      } else {
-        const int a = c_hrow[tid - 6], b = c_hcol[tid - 6];
-        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-        if (b < 3) {  // rotation - rotation
-          const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
-          const double gn = Cent(s, a2, b2, a1, b1) - Cent(s, a2, b1, a1, b2) - Cent(s, a1, b2, a2, b1) +
-                            Cent(s, a1, b1, a2, b2);
-          const double trN = s.NM[0] + s.NM[5] + s.NM[10];
-          v = 2.0 * gn + s.NM[4 * a + b] + s.NM[4 * b + a] - (a == b ? 2.0 * trN : 0.0);
-        } else if (a < 3) {  // rotation a - translation c
-          const int c = b - 3;
-          const double gn = Cent(s, a1, 3, a2, c) - Cent(s, a2, 3, a1, c);
-          double sec = 0.0;
-          if (c != a) {
-            const int i = 3 - a - c;
-            sec = eps3(a, c, i) * s.NM[4 * i + 3];
-          }
-          v = 2.0 * gn + sec;
-        } else {  // translation - translation
-          v = 2.0 * Cent(s, 3, 3, a - 3, b - 3);
-        }
-      }
+      const double* Cf = &s.C[0][0];
+      double v = 0.0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v = fma(c_hess.cc[tid][t], Cf[c_hess.ic[tid][t]], v);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) v = fma(c_hess.cn[tid][t], s.NM[c_hess.in[tid][t]], v);
       s.gH[tid] = v;
       s.gHf[tid] = static_cast<float>(v);
     }
@@ -302,7 +365,8 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         const int k = tid / 3, j = tid % 3;
         const double* w = s.wv;
         const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        const double Wkj = -(eps3(k, j, 0) * w[0] + eps3(k, j, 1) * w[1] + eps3(k, j, 2) * w[2]);
+        // ([w]x)_kj = -eps_kjm w_m (m = 3 - k - j; zero on the diagonal)
+        const double Wkj = (k == j) ? 0.0 : -eps3(k, j, 3 - k - j) * w[3 - k - j];
         const double W2kj = w[k] * w[j] - (k == j ? th2 : 0.0);
         s.E[tid] = (k == j ? 1.0 : 0.0) + s.coef[0] * Wkj + s.coef[1] * W2kj;
       } else if (tid >= 32 && tid < 35) {
@@ -331,11 +395,15 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         double dq = 0.0;
         if (tid < 12) {
           const int i = tid / 4, k = tid % 4;
-          double g = 0.0;
+          double gl[4];
 #pragma unroll
-          for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int l = 0; l < 4; ++l) g += Aent(s, pair_q(k, l), i, j) * s.dl[4 * j + l];
+          for (int l = 0; l < 4; ++l) {  // four independent chains of three
+            const double* Aq = s.A[pair_q(k, l)];
+            gl[l] = Aq[sym_p(i, 0)] * s.dl[l];
+            gl[l] = fma(Aq[sym_p(i, 1)], s.dl[4 + l], gl[l]);
+            gl[l] = fma(Aq[sym_p(i, 2)], s.dl[8 + l], gl[l]);
+          }
+          const double g = (gl[0] + gl[1]) + (gl[2] + gl[3]);
           s.Gd[tid] = g;
           dq = s.dl[tid] * (2.0 * s.M1[tid] + g);
         }
@@ -365,9 +433,10 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       __syncthreads();
     }
     if (tid == 0) {
-      double nx = 0.0;
-      for (int a = 0; a < 6; ++a) nx += s.wv[a] * s.wv[a];
-      if (!s.accepted || sqrt(nx) < newton_tol) s.go = 0;
+      float nx = 0.f;  // |step xi|^2 of the accepted step (FP32 suffices for the test)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) nx += static_cast<float>(step) * s.xf[a] * (static_cast<float>(step) * s.xf[a]);
+      if (!s.accepted || nx < static_cast<float>(newton_tol) * static_cast<float>(newton_tol)) s.go = 0;
     }
     __syncthreads();
     if (!s.go) break;

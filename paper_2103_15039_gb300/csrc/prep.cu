@@ -221,70 +221,100 @@ __global__ void to_float4_kernel(const float* __restrict__ Y, long long M, float
   if (i < M) y4[i] = make_float4(Y[3 * i], Y[3 * i + 1], Y[3 * i + 2], 0.f);
 }
 
+// Insert (d, ci) into the sorted first k entries of (bd, bi); an equal distance
+// already present (lower index) stays first.  Fully unrolled over KMAX.
 template <int KMAX>
+__device__ __forceinline__ void knn_insert(float (&bd)[KMAX], int (&bi)[KMAX], float& thr, int k, float d,
+                                           int ci) {
+#pragma unroll
+  for (int s = KMAX - 1; s >= 0; --s) {
+    if (s < k) {
+      if (s > 0 && bd[s - 1] > d) {
+        bd[s] = bd[s - 1];
+        bi[s] = bi[s - 1];
+      } else if (bd[s] > d) {
+        bd[s] = d;
+        bi[s] = ci;
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < KMAX; ++s)
+    if (s == k - 1) thr = bd[s];
+}
+
+// Two queries per thread (q and q + kKnnThreads), packed FP32x2 distances:
+// with the candidate stored negated, p + (-c) is exactly p - c, and
+// fma(dz, dz, fma(dy, dy, dx * dx)) per half is the scalar formula.
+// KFIX > 0: k == KFIX is a compile-time constant (lists stay in registers);
+// KFIX == 0: runtime k <= KMAX.
+template <int KMAX, int KFIX>
 __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* __restrict__ y4, long long M,
-                                                                  int k, int splits,
+                                                                  int k_rt, int splits,
                                                                   float* __restrict__ part_d,
                                                                   int* __restrict__ part_i) {
-  __shared__ float4 cand[kKnnTile];
-  const long long q = static_cast<long long>(blockIdx.x) * kKnnThreads + threadIdx.x;
+  const int k = KFIX > 0 ? KFIX : k_rt;
+  __shared__ float4 cxy[kKnnTile];  // (-x, -x, -y, -y)
+  __shared__ float2 cz[kKnnTile];   // (-z, -z)
+  const long long q0 = static_cast<long long>(blockIdx.x) * (2 * kKnnThreads) + threadIdx.x;
+  const long long q1 = q0 + kKnnThreads;
   const int split = blockIdx.y;
   const long long per = (M + splits - 1) / splits;
   const long long c_lo = split * per;
   long long c_hi = c_lo + per;
   if (c_hi > M) c_hi = M;
-  const bool valid = q < M;
-  const float4 p = valid ? y4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float bd[KMAX];
-  int bi[KMAX];
+  const bool v0 = q0 < M, v1 = q1 < M;
+  const float4 p0 = v0 ? y4[q0] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 p1 = v1 ? y4[q1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 px = make_float2(p0.x, p1.x), py = make_float2(p0.y, p1.y), pz = make_float2(p0.z, p1.z);
+  float bd0[KMAX], bd1[KMAX];
+  int bi0[KMAX], bi1[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
-    bd[j] = INFINITY;
-    bi[j] = 0x7fffffff;
+    bd0[j] = bd1[j] = INFINITY;
+    bi0[j] = bi1[j] = 0x7fffffff;
   }
-  float thr = INFINITY;  // current k-th best
+  float thr0 = INFINITY, thr1 = INFINITY;
   for (long long base = c_lo; base < c_hi; base += kKnnTile) {
     const int cnt = static_cast<int>((c_hi - base) < kKnnTile ? (c_hi - base) : kKnnTile);
     __syncthreads();
-    for (int j = threadIdx.x; j < cnt; j += kKnnThreads) cand[j] = y4[base + j];
+    for (int j = threadIdx.x; j < cnt; j += kKnnThreads) {
+      const float4 c = y4[base + j];
+      cxy[j] = make_float4(-c.x, -c.x, -c.y, -c.y);
+      cz[j] = make_float2(-c.z, -c.z);
+    }
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
-      const float4 c = cand[j];
-      const float dx = __fsub_rn(p.x, c.x);
-      const float dy = __fsub_rn(p.y, c.y);
-      const float dz = __fsub_rn(p.z, c.z);
-      const float d = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-      if (d < thr) {
-        const int ci = static_cast<int>(base + j);
-        // insert (d, ci) into the sorted list of the first k entries; an equal
-        // distance already present (lower index) stays first
-#pragma unroll
-        for (int s = KMAX - 1; s >= 0; --s) {
-          if (s < k) {
-            if (s > 0 && bd[s - 1] > d) {
-              bd[s] = bd[s - 1];
-              bi[s] = bi[s - 1];
-            } else if (bd[s] > d) {
-              bd[s] = d;
-              bi[s] = ci;
-            }
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < KMAX; ++s)
-          if (s == k - 1) thr = bd[s];
-      }
+      const float4 a = cxy[j];
+      const float2 dx = __fadd2_rn(px, make_float2(a.x, a.y));
+      const float2 dy = __fadd2_rn(py, make_float2(a.z, a.w));
+      const float2 dz = __fadd2_rn(pz, cz[j]);
+      const float2 d = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+      const int ci = static_cast<int>(base + j);
+      if (d.x < thr0) knn_insert<KMAX>(bd0, bi0, thr0, k, d.x, ci);
+      if (d.y < thr1) knn_insert<KMAX>(bd1, bi1, thr1, k, d.y, ci);
     }
   }
-  if (!valid) return;
-  float* od = part_d + (static_cast<size_t>(split) * M + q) * k;
-  int* oi = part_i + (static_cast<size_t>(split) * M + q) * k;
+  if (v0) {
+    float* od = part_d + (static_cast<size_t>(split) * M + q0) * k;
+    int* oi = part_i + (static_cast<size_t>(split) * M + q0) * k;
 #pragma unroll
-  for (int s = 0; s < KMAX; ++s)
-    if (s < k) {
-      od[s] = bd[s];
-      oi[s] = bi[s];
-    }
+    for (int s = 0; s < KMAX; ++s)
+      if (s < k) {
+        od[s] = bd0[s];
+        oi[s] = bi0[s];
+      }
+  }
+  if (v1) {
+    float* od = part_d + (static_cast<size_t>(split) * M + q1) * k;
+    int* oi = part_i + (static_cast<size_t>(split) * M + q1) * k;
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s)
+      if (s < k) {
+        od[s] = bd1[s];
+        oi[s] = bi1[s];
+      }
+  }
 }
 
 // Merge the sorted partial lists of every split by (distance, index).
@@ -476,7 +506,7 @@ cudaError_t launch_init(const float* X, int64_t N, const float* Y, int64_t M, co
 }
 
 int knn_splits(int64_t M, int num_sms) {
-  const long long qblocks = (M + kKnnThreads - 1) / kKnnThreads;
+  const long long qblocks = (M + 2 * kKnnThreads - 1) / (2 * kKnnThreads);
   long long sp = (4LL * num_sms + qblocks - 1) / qblocks;
   if (sp < 1) sp = 1;
   if (sp > 32) sp = 32;
@@ -488,11 +518,19 @@ int knn_splits(int64_t M, int num_sms) {
 cudaError_t launch_knn(const float* Y, int64_t M, int k, float4* y4, float* part_d, int* part_i,
                        int* idx_out, int splits, cudaStream_t s) {
   to_float4_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, s>>>(Y, M, y4);
-  dim3 grid(static_cast<unsigned>((M + kKnnThreads - 1) / kKnnThreads), static_cast<unsigned>(splits));
-  if (k <= 16)
-    knn_partial_kernel<16><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
-  else
-    knn_partial_kernel<32><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
+  dim3 grid(static_cast<unsigned>((M + 2 * kKnnThreads - 1) / (2 * kKnnThreads)), static_cast<unsigned>(splits));
+  switch (k) {
+#define LSG_KNN_CASE(K) \
+  case K:               \
+    knn_partial_kernel<K, K><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i); \
+    break;
+    LSG_KNN_CASE(1) LSG_KNN_CASE(2) LSG_KNN_CASE(3) LSG_KNN_CASE(4) LSG_KNN_CASE(5) LSG_KNN_CASE(6)
+    LSG_KNN_CASE(7) LSG_KNN_CASE(8) LSG_KNN_CASE(9) LSG_KNN_CASE(10) LSG_KNN_CASE(11) LSG_KNN_CASE(12)
+    LSG_KNN_CASE(13) LSG_KNN_CASE(14) LSG_KNN_CASE(15) LSG_KNN_CASE(16)
+#undef LSG_KNN_CASE
+    default:
+      knn_partial_kernel<32, 0><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
+  }
   knn_merge_kernel<<<static_cast<unsigned>((M + 127) / 128), 128, 0, s>>>(part_d, part_i, M, k, splits,
                                                                          idx_out);
   return cudaGetLastError();

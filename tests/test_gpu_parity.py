@@ -160,3 +160,21 @@ def test_invalid_arguments_report_einval(ctx):
         ctx.register(np.random.rand(5, 3).astype(np.float32), np.random.rand(50, 3).astype(np.float32),
                      binding.default_params(w=1.0))
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("k", [1, 4, 16, 20, 32])
+def test_knn_other_neighbourhood_sizes(ctx, k):
+    """Exact neighbour lists for compile-time (k <= 16) and runtime (k > 16) kernels."""
+    Y = synth.sphere_plane_pair(seed=6, n=10, m=1500)["Y"]
+    p = binding.default_params(knn_k=k)
+    g = ctx.preprocess(_cuda(Y), p, want_idx=True)
+    np.testing.assert_array_equal(g["idx"].cpu().numpy(), oracle.knn(Y, k))
+
+
+def test_knn_exact_ties_keep_the_lower_index(ctx):
+    """A lattice has many exactly equal FP32 distances; ties must go to the lower index."""
+    g1 = np.arange(6, dtype=np.float32)
+    Y = np.stack(np.meshgrid(g1, g1, g1, indexing="ij"), axis=-1).reshape(-1, 3).astype(np.float32)
+    p = binding.default_params(knn_k=7)
+    g = ctx.preprocess(_cuda(Y), p, want_idx=True)
+    np.testing.assert_array_equal(g["idx"].cpu().numpy(), oracle.knn(Y, 7))
