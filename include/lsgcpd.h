@@ -55,7 +55,7 @@ typedef enum {
 /* Global E-step moments returned by lsgcpd_estep (doubles):
  *   [0]      N_P = sum_n Pbar_n
  *   [1]      sum_n D_n
- *   [2..13]  H1 (3x4 row-major) = sum_n h_n xt_n^T,  h_n = rho_n + beta_n
+ *   [2..13]  H1 (3x4 row-major) = sum_n h_n xt_n^T
  *   [14..73] G = sum_n A_n (x) xt_n xt_n^T, A_n = Pbar_n I + W_n, 60 unique
  *            entries ordered by A pair (00,01,02,11,12,22) major and
  *            xt pair (00,01,02,03,11,12,13,22,23,33) minor
@@ -145,11 +145,11 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* ctx, const float* Y, int64_t M, cons
  *   R, t    host, the pose at which the posteriors are evaluated
  *   sigma2  > 0;  volume > 0 (V of p_o = 1/V)
  *   moments host, LSGCPD_MOMENTS doubles (output) or NULL
- *   per_n   device, N x LSGCPD_PER_N_WIDTH FP32 (output) or NULL, per source n:
- *           [0] Pbar = sum_m P_mn, [1..3] rho = sum_m P_mn r_mn (r = z_n - y_m),
+ *   per_n   device, N x LSGCPD_PER_N_WIDTH FP32 (output) or NULL, per source n,
+ *           with r_mn = z_n - y_m and Lambda_m = I + alpha_m n_m n_m^T:
+ *           [0] Pbar = sum_m P_mn, [1..3] h = sum_m P_mn Lambda_m r_mn,
  *           [4..9] W = sum_m P_mn alpha_m n_m n_m^T (00,01,02,11,12,22),
- *           [10..12] beta = sum_m P_mn alpha_m (n_m . r_mn) n_m,
- *           [13] D = sum_m P_mn d_mn, d = |r|^2 + alpha (n . r)^2, [14] Pout, [15] 0.
+ *           [10] D = sum_m P_mn d_mn, d = r^T Lambda_m r, [11] Pout, [12..15] 0.
  * Uses p->w (0 allowed: no outlier term) and p->include_alpha_norm. */
 lsgcpd_status lsgcpd_estep(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y,
                            const float* normals, const float* alpha, int64_t M,

@@ -1,24 +1,24 @@
 // E step of LSG-CPD on sm_103a (Eq. (5) evaluated in the form of Eq. (9)).
 //
 // For every source n and every target m (Eq. (2)):
-//   r_mn = z_n - y_m,  d_mn = |r|^2 + alpha_m (n_m . r)^2 = |r|^2 + (a_m . r)^2,  a = sqrt(alpha) n
-//   P_mn = pi_m e^{-d/(2 s2)} / (sum_k pi_k e^{-d_k/(2 s2)} + gamma_n),
+//   r_mn = z_n - y_m,  d_mn = |r|^2 + alpha_m (n_m . r)^2 = r . u,  u = Lambda_m r = r + (a_m . r) a_m,
+//   a = sqrt(alpha) n,  P_mn = pi_m e^{-d/(2 s2)} / (sum_k pi_k e^{-d_k/(2 s2)} + gamma_n),
 //   gamma_n = w/(1-w) (2 pi s2)^{3/2} / V.
 // The kernel never forms P.  It evaluates e_mn = 2^(l_m - c d_mn - L_n) with
-// c = log2(e)/(2 s2) and a per-source shift L_n, and accumulates 14 per-source
-// moments (S0, rho, W, beta, D') from which the normalised posteriors'
-// sufficient statistics follow by one division (combine kernel below):
-//   S0 = sum e, rho = sum e r, W = sum e a a^T, beta = sum e (a.r) a,
+// c = log2(e)/(2 s2) and a per-source shift L_n, and accumulates 11 per-source
+// moments from which the M step's sufficient statistics follow by one division
+// (combine kernel below):
+//   S0 = sum e, h = sum e u (= rho + beta of the residual form), W = sum e a a^T,
 //   D' = sum e (d + kappa_n),  kappa_n = L_n / c.
 // Folding kappa_n into the squared distance makes the shift free in the hot
 // loop; the combine subtracts kappa_n S0.
 //
 // Hot-loop layout (GB300):
 //  * a CTA = 4 warps; each thread owns S sources (z_n duplicated into both
-//    halves of an FP32x2 register) and 14 FP32x2 accumulators per source;
+//    halves of an FP32x2 register) and 11 FP32x2 accumulators per source;
 //  * the two halves of every packed register belong to two consecutive
 //    targets, so every operation of the pair update is one packed
-//    FADD2/FMUL2/FFMA2 (26 per target pair per source) plus two MUFU.EX2;
+//    FADD2/FMUL2/FFMA2 (24 per target pair per source) plus two MUFU.EX2;
 //  * target tiles (kTile records, 6.5 KB) stream into a 4-stage shared-memory
 //    ring by cp.async.bulk (TMA bulk copy) completing on mbarriers; every warp
 //    reads the tile with broadcast 128-bit shared loads;
@@ -90,7 +90,7 @@ struct Src {
 };
 
 struct Acc {
-  float2 s0, r0, r1, r2, w00, w01, w02, w11, w12, w22, b0, b1, b2, d;
+  float2 s0, h0, h1, h2, w00, w01, w02, w11, w12, w22, d;
 };
 
 struct Tgt {  // two consecutive targets, one per half
@@ -99,36 +99,34 @@ struct Tgt {  // two consecutive targets, one per half
 
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
-// One source against two targets: 26 packed FP32 operations and 2 EX2.
+// One source against two targets: 24 packed FP32 operations and 2 EX2.
 __device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g, float2 nc) {
   const float2 r0 = __fadd2_rn(s.z0, g.ny0);
   const float2 r1 = __fadd2_rn(s.z1, g.ny1);
   const float2 r2 = __fadd2_rn(s.z2, g.ny2);
-  float2 dd = __ffma2_rn(r2, r2, s.kp);
-  dd = __ffma2_rn(r1, r1, dd);
-  dd = __ffma2_rn(r0, r0, dd);
-  float2 v = __fmul2_rn(g.a0, r0);
+  float2 v = __fmul2_rn(g.a0, r0);  // v = a . r
   v = __ffma2_rn(g.a1, r1, v);
   v = __ffma2_rn(g.a2, r2, v);
-  dd = __ffma2_rn(v, v, dd);                 // d + kappa_n
+  const float2 u0 = __ffma2_rn(v, g.a0, r0);  // u = r + v a = Lambda r
+  const float2 u1 = __ffma2_rn(v, g.a1, r1);
+  const float2 u2 = __ffma2_rn(v, g.a2, r2);
+  float2 dd = __ffma2_rn(r2, u2, s.kp);  // d + kappa_n = r . u + kappa_n
+  dd = __ffma2_rn(r1, u1, dd);
+  dd = __ffma2_rn(r0, u0, dd);
   const float2 x = __ffma2_rn(dd, nc, g.l);  // l_m - c (d + kappa_n)
   float2 e;
   e.x = ex2_approx(x.x);
   e.y = ex2_approx(x.y);
   A.s0 = __fadd2_rn(A.s0, e);
-  A.r0 = __ffma2_rn(e, r0, A.r0);
-  A.r1 = __ffma2_rn(e, r1, A.r1);
-  A.r2 = __ffma2_rn(e, r2, A.r2);
+  A.h0 = __ffma2_rn(e, u0, A.h0);
+  A.h1 = __ffma2_rn(e, u1, A.h1);
+  A.h2 = __ffma2_rn(e, u2, A.h2);
   A.w00 = __ffma2_rn(e, g.q00, A.w00);
   A.w01 = __ffma2_rn(e, g.q01, A.w01);
   A.w02 = __ffma2_rn(e, g.q02, A.w02);
   A.w11 = __ffma2_rn(e, g.q11, A.w11);
   A.w12 = __ffma2_rn(e, g.q12, A.w12);
   A.w22 = __ffma2_rn(e, g.q22, A.w22);
-  const float2 ev = __fmul2_rn(e, v);
-  A.b0 = __ffma2_rn(ev, g.a0, A.b0);
-  A.b1 = __ffma2_rn(ev, g.a1, A.b1);
-  A.b2 = __ffma2_rn(ev, g.a2, A.b2);
   A.d = __ffma2_rn(e, dd, A.d);
 }
 
@@ -169,19 +167,16 @@ __device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)
 
 __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc& a) {
   dst[0 * SB + nl] = a.s0.x + a.s0.y;
-  dst[1 * SB + nl] = a.r0.x + a.r0.y;
-  dst[2 * SB + nl] = a.r1.x + a.r1.y;
-  dst[3 * SB + nl] = a.r2.x + a.r2.y;
+  dst[1 * SB + nl] = a.h0.x + a.h0.y;
+  dst[2 * SB + nl] = a.h1.x + a.h1.y;
+  dst[3 * SB + nl] = a.h2.x + a.h2.y;
   dst[4 * SB + nl] = a.w00.x + a.w00.y;
   dst[5 * SB + nl] = a.w01.x + a.w01.y;
   dst[6 * SB + nl] = a.w02.x + a.w02.y;
   dst[7 * SB + nl] = a.w11.x + a.w11.y;
   dst[8 * SB + nl] = a.w12.x + a.w12.y;
   dst[9 * SB + nl] = a.w22.x + a.w22.y;
-  dst[10 * SB + nl] = a.b0.x + a.b0.y;
-  dst[11 * SB + nl] = a.b1.x + a.b1.y;
-  dst[12 * SB + nl] = a.b2.x + a.b2.y;
-  dst[13 * SB + nl] = a.d.x + a.d.y;
+  dst[10 * SB + nl] = a.d.x + a.d.y;
 }
 
 template <int S>
@@ -252,7 +247,7 @@ __global__ void __launch_bounds__(kNW * 32, (S >= 4 ? 2 : 3))
       src[s].z2 = dup(z2);
       src[s].kp = dup(kap_n ? kap_n[n] : kap_uniform);
       const float2 zero = make_float2(0.f, 0.f);
-      acc[s] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
+      acc[s] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
     }
 
     for (; u < seg_end; ++u, ++i) {
@@ -404,25 +399,23 @@ __global__ void __launch_bounds__(kCombineThreads)
       }
     }
     const float S0 = m[0];
-    const float D = m[13] - kap * S0;
+    const float D = m[10] - kap * S0;
     const float denom = S0 + gp;
     const float inv = denom > 0.f ? 1.f / denom : 0.f;
     const float Pb = S0 * inv;
-    const float r0 = m[1] * inv, r1 = m[2] * inv, r2 = m[3] * inv;
+    const float h[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
     const float W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv,
                 W12 = m[8] * inv, W22 = m[9] * inv;
-    const float be0 = m[10] * inv, be1 = m[11] * inv, be2 = m[12] * inv;
     const float Dn = D * inv;
     const float Pout = gp * inv;
     const float nll = (valid && denom > 0.f) ? nll_c - (L * 0.6931471805599453f + logf(denom)) : 0.f;
     if (valid && per_n) {
       float4* o = reinterpret_cast<float4*>(per_n + n * 16);
-      o[0] = make_float4(Pb, r0, r1, r2);
+      o[0] = make_float4(Pb, h[0], h[1], h[2]);
       o[1] = make_float4(W00, W01, W02, W11);
-      o[2] = make_float4(W12, W22, be0, be1);
-      o[3] = make_float4(be2, Dn, Pout, 0.f);
+      o[2] = make_float4(W12, W22, Dn, Pout);
+      o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const float h[3] = {r0 + be0, r1 + be1, r2 + be2};
     const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
     const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
     row[0] = Pb;

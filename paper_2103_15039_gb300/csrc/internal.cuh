@@ -23,9 +23,9 @@ constexpr int kTileFloats = kPlanes * kTile;
 constexpr int kTileBytes = kTileFloats * 4;
 
 // Per-source raw E-step moments accumulated by the hot kernel:
-//   S0 = sum e, rho (3) = sum e r, W (6) = sum e a a^T, beta (3) = sum e (a.r) a,
+//   S0 = sum e, h (3) = sum e Lambda_m r (Lambda_m = I + a a^T), W (6) = sum e a a^T,
 //   D' = sum e (d + kappa_n)
-constexpr int kMom = 14;
+constexpr int kMom = 11;
 
 // Global moments (see lsgcpd.h): N_P, sum D, H1 (12), G (60), sum Pout, NLL part.
 constexpr int kGlob = 76;

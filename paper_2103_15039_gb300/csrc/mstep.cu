@@ -6,7 +6,7 @@
 // (3x4).  With x~ = [x; 1] and the transform T_o used by the E step,
 //   Q_d(T) = SD + 2 <H1, T - T_o> + <T - T_o, G (T - T_o)>,
 //   H1 = sum_n h_n x~_n^T,  G_(ik),(jl) = A^{kl}_ij = sum_n A_n,ij x~_nk x~_nl,
-// (h_n = rho_n + beta_n, A_n = Pbar_n I + W_n), so the inner Newton loop of
+// (h_n = sum_m P_mn Lambda_m r_mn, A_n = Pbar_n I + W_n), so the inner Newton loop of
 // Eq. (13) costs O(1) per step, independent of N and M.
 //
 // Newton on SE(3): right perturbation T o exp(xi^), basis order rotations
@@ -134,13 +134,6 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
 
 __constant__ HessTab c_hess = make_hess_tab();
 
-// position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
-__host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
-
-// row / column of the i-th entry of the upper triangle of a 6x6 matrix
-__constant__ int c_hrow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
-__constant__ int c_hcol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
-
 struct Shared {
   double SD, NP;
   double H1[12];
@@ -163,7 +156,18 @@ struct Shared {
   int iters, damped, halvings;
   int go;          // loop control
   int accepted;
+  HessTab hess;    // per-lane divergent lookups: shared, not constant, memory
+  double series[3][9];
 };
+
+// position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
+__host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
+
+// row / column of the i-th entry of the upper triangle of a 6x6 matrix
+__constant__ int c_hrow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ int c_hcol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
+
 
 __device__ __forceinline__ int pair_q(int k, int l) {
   if (k > l) {
@@ -197,6 +201,12 @@ __device__ __forceinline__ double eps3(int a, int b, int c) {
 
 __device__ void load_model(Shared& s, const double* mom) {
   const int tid = threadIdx.x;
+  {
+    const int* src = reinterpret_cast<const int*>(&c_hess);
+    int* dst = reinterpret_cast<int*>(&s.hess);
+    for (int i = tid; i < static_cast<int>(sizeof(HessTab) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    if (tid < 27) s.series[tid / 9][tid % 9] = c_exp_series[tid / 9][tid % 9];
+  }
   if (tid == 0) {
     s.NP = mom[0];
     s.SD = mom[1];
@@ -258,6 +268,16 @@ __device__ __forceinline__ bool ldl_solve6(const float (&H)[36], const float (&b
 // Newton loop on the model in shared memory; T starts at (s.R, s.t) == (s.Ro, s.to).
 __device__ void newton(Shared& s, int newton_max, double newton_tol) {
   const int tid = threadIdx.x;
+  // lane tid < 12 owns (G D)_ik, i = tid / 4, k = tid % 4: its 12 model entries
+  // A^{q(k,l)}_{i j} (j = 0..2, l = 0..3) are fixed, so their flat offsets are too
+  int gidx[12];
+  {
+    const int i = (tid / 4) % 3, k = tid % 4;
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) gidx[3 * l + j] = pair_q(k, l) * 6 + sym_p(i, j);
+  }
   if (tid < 12) s.M1[tid] = s.H1[tid];
   if (tid == 0) {
     s.Q = s.SD;
@@ -290,9 +310,9 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       const double* Cf = &s.C[0][0];
       double v = 0.0;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) v = fma(c_hess.cc[tid][t], Cf[c_hess.ic[tid][t]], v);
+      for (int t = 0; t < 4; ++t) v = fma(s.hess.cc[tid][t], Cf[s.hess.ic[tid][t]], v);
 #pragma unroll
-      for (int t = 0; t < 3; ++t) v = fma(c_hess.cn[tid][t], s.NM[c_hess.in[tid][t]], v);
+      for (int t = 0; t < 3; ++t) v = fma(s.hess.cn[tid][t], s.NM[s.hess.in[tid][t]], v);
       s.gH[tid] = v;
       s.gHf[tid] = static_cast<float>(v);
     }
@@ -326,8 +346,15 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         s.go = 0;
       } else {
         ++s.iters;
+        float nx = 0.f;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) s.xf[a] = x[a];
+        for (int a = 0; a < 6; ++a) {
+          s.xf[a] = x[a];
+          nx += x[a] * x[a];
+        }
+        // a step below the tolerance changes the transform by less than the tolerance:
+        // the iteration has converged, so it is not evaluated
+        if (nx < static_cast<float>(newton_tol) * static_cast<float>(newton_tol)) s.go = 0;
       }
       s.accepted = 0;
     }
@@ -345,7 +372,7 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         const double x = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
         double cf;
         if (x <= 0.25) {
-          const double* c = c_exp_series[tid];
+          const double* c = s.series[tid];
           double r = c[8];
 #pragma unroll
           for (int k = 7; k >= 0; --k) r = fma(r, x, c[k]);
@@ -395,13 +422,13 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         double dq = 0.0;
         if (tid < 12) {
           const int i = tid / 4, k = tid % 4;
+          const double* Af = &s.A[0][0];
           double gl[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {  // four independent chains of three
-            const double* Aq = s.A[pair_q(k, l)];
-            gl[l] = Aq[sym_p(i, 0)] * s.dl[l];
-            gl[l] = fma(Aq[sym_p(i, 1)], s.dl[4 + l], gl[l]);
-            gl[l] = fma(Aq[sym_p(i, 2)], s.dl[8 + l], gl[l]);
+            gl[l] = Af[gidx[3 * l]] * s.dl[l];
+            gl[l] = fma(Af[gidx[3 * l + 1]], s.dl[4 + l], gl[l]);
+            gl[l] = fma(Af[gidx[3 * l + 2]], s.dl[8 + l], gl[l]);
           }
           const double g = (gl[0] + gl[1]) + (gl[2] + gl[3]);
           s.Gd[tid] = g;

@@ -3,10 +3,9 @@ CUDA library reports.  FP64 numpy; shares nothing with the CUDA path.
 
 The oracle gives, per source n, Pbar, ybar = sum P y, W = sum P alpha n n^T,
 b = sum P alpha (n.y) n, f = sum P (|y|^2 + alpha (n.y)^2), Pout.  With
-z = R x + t and e = ybar + b, A = Pbar I + W:
-  rho  = sum P (z - y)                 = Pbar z - ybar
-  beta = sum P alpha (n.(z - y)) n     = W z - b
-  D    = sum P d(z)                    = z^T A z - 2 e^T z + f
+z = R x + t, A = Pbar I + W, e = ybar + b and Lambda_m = I + alpha_m n_m n_m^T:
+  h = sum P Lambda_m (z - y_m)  = A z - e
+  D = sum P d(z)                = z^T A z - 2 e^T z + f
 """
 import numpy as np
 
@@ -15,6 +14,7 @@ XT_PAIRS = [(k, l) for k in range(4) for l in range(k, 4)]
 
 
 def per_source(stats, X, R, t):
+    """Per-source layout of the library: Pbar, h (3), W (6), D, Pout, 0 x 4."""
     s = np.asarray(stats, dtype=np.float64)
     Z = np.asarray(X, dtype=np.float64) @ np.asarray(R).reshape(3, 3).T + np.asarray(t).ravel()
     N = len(Z)
@@ -27,11 +27,10 @@ def per_source(stats, X, R, t):
     A = W + Pb[:, None, None] * np.eye(3)[None]
     e = s[:, 1:4] + s[:, 10:13]
     out[:, 0] = Pb
-    out[:, 1:4] = Pb[:, None] * Z - s[:, 1:4]
+    out[:, 1:4] = np.einsum("nij,nj->ni", A, Z) - e
     out[:, 4:10] = s[:, 4:10]
-    out[:, 10:13] = np.einsum("nij,nj->ni", W, Z) - s[:, 10:13]
-    out[:, 13] = np.einsum("ni,nij,nj->n", Z, A, Z) - 2 * np.einsum("ni,ni->n", e, Z) + s[:, 13]
-    out[:, 14] = s[:, 14]
+    out[:, 10] = np.einsum("ni,nij,nj->n", Z, A, Z) - 2 * np.einsum("ni,ni->n", e, Z) + s[:, 13]
+    out[:, 11] = s[:, 14]
     return out
 
 
@@ -39,18 +38,18 @@ def global_moments(per_n, X, nll):
     """The 76 global moments from per-source residual-form moments (caller's frame)."""
     p = np.asarray(per_n, dtype=np.float64)
     Xt = np.concatenate([np.asarray(X, dtype=np.float64), np.ones((len(p), 1))], axis=1)
-    h = p[:, 1:4] + p[:, 10:13]
+    h = p[:, 1:4]
     Avals = [p[:, 0] + p[:, 4], p[:, 5], p[:, 6], p[:, 0] + p[:, 7], p[:, 8], p[:, 0] + p[:, 9]]
     m = np.zeros(76)
     m[0] = p[:, 0].sum()
-    m[1] = p[:, 13].sum()
+    m[1] = p[:, 10].sum()
     m[2:14] = np.einsum("ni,nk->ik", h, Xt).ravel()
     j = 14
     for a in Avals:
         for (k, l) in XT_PAIRS:
             m[j] = (a * Xt[:, k] * Xt[:, l]).sum()
             j += 1
-    m[74] = p[:, 14].sum()
+    m[74] = p[:, 11].sum()
     m[75] = nll
     return m
 
