@@ -177,6 +177,40 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const 
                               const lsgcpd_params* p, lsgcpd_result* out, double* trace,
                               void* stream);
 
+/* Size limits and scratch size of lsgcpd_estep_noalloc. */
+#define LSGCPD_NOALLOC_MAX_N 4096
+#define LSGCPD_NOALLOC_MAX_M 4096
+#define LSGCPD_NOALLOC_ARENA_BYTES (16u << 20)
+
+/* The E step of lsgcpd_estep for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of the same
+ * computation (same kernels, same results as lsgcpd_estep).
+ *
+ * Who needs it: code that runs while another framework owns the device memory
+ * pool, latency-critical loops in which cudaMalloc/cudaFree would synchronise
+ * the device, and integrations that must keep a fixed, known footprint.  It
+ * takes no context (creating one allocates) and calls no cudaMalloc, cudaFree
+ * or allocating library routine.  All scratch memory lives in one
+ * LSGCPD_NOALLOC_ARENA_BYTES static device array that every GPU which loads
+ * the library holds until the process exits.
+ *
+ * Arguments and outputs are those of lsgcpd_estep (X, Y, normals, alpha,
+ * per_n: device memory of the calling thread's current device; R, t, moments:
+ * host).  moments must not be NULL.  Returns EINVAL if N or M exceeds
+ * LSGCPD_NOALLOC_MAX_N / LSGCPD_NOALLOC_MAX_M or an argument is invalid;
+ * no error message is kept (there is no context).
+ *
+ * The first call on a device looks the arena's device address up
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  Every call shares the one arena and leaves its contents
+ * behind: concurrent or overlapping calls (other threads, other streams whose
+ * work has not finished) race on it and must be serialised by the caller.
+ * The call synchronises `stream` before returning. */
+lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const float* Y, const float* normals,
+                                   const float* alpha, int64_t M, const lsgcpd_params* p,
+                                   const double R[9], const double t[3], double sigma2, double volume,
+                                   double* moments, float* per_n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

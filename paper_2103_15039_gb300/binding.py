@@ -77,6 +77,9 @@ def lib():
         L.lsgcpd_mstep.restype = C.c_int
         L.lsgcpd_register.argtypes = [vp, fp, i64, fp, i64, C.POINTER(Params), C.POINTER(Result), dp, vp]
         L.lsgcpd_register.restype = C.c_int
+        L.lsgcpd_estep_noalloc.argtypes = [fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
+                                           C.c_double, dp, fp, vp]
+        L.lsgcpd_estep_noalloc.restype = C.c_int
         _lib = L
     return _lib
 
@@ -196,6 +199,30 @@ def lsgcpd_estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=
                             float(volume), mom.ctypes.data_as(dpp),
                             C.c_void_p(pn.data_ptr()) if pn is not None else None, _stream(stream))
     _check(ctx, rc)
+    return dict(moments=mom, per_n=pn)
+
+
+def lsgcpd_estep_noalloc(X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None):
+    """The E step without a context and without any device allocation by the library
+    (fixed-size static scratch; see lsgcpd.h).  `per_n`, if requested, is allocated
+    here by torch, i.e. by the caller."""
+    import torch
+    N, M = X.shape[0], Y.shape[0]
+    _dev_ptr(X, "X", (N, 3))
+    _dev_ptr(Y, "Y", (M, 3))
+    _dev_ptr(normals, "normals", (M, 3))
+    _dev_ptr(alpha, "alpha", (M,))
+    Rd, td = _d(R, 9), _d(t, 3)
+    mom = np.zeros(MOMENTS)
+    pn = torch.empty((N, PER_N_WIDTH), dtype=torch.float32, device=X.device) if per_n else None
+    dpp = C.POINTER(C.c_double)
+    rc = lib().lsgcpd_estep_noalloc(C.c_void_p(X.data_ptr()), N, C.c_void_p(Y.data_ptr()),
+                                    C.c_void_p(normals.data_ptr()), C.c_void_p(alpha.data_ptr()), M,
+                                    C.byref(params), Rd.ctypes.data_as(dpp), td.ctypes.data_as(dpp),
+                                    float(sigma2), float(volume), mom.ctypes.data_as(dpp),
+                                    C.c_void_p(pn.data_ptr()) if pn is not None else None, _stream(stream))
+    if rc != 0:
+        raise LsgcpdError(rc, "lsgcpd_estep_noalloc failed")
     return dict(moments=mom, per_n=pn)
 
 
