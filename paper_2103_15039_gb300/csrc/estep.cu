@@ -14,7 +14,7 @@
 // loop; the combine subtracts kappa_n S0.
 //
 // Hot-loop layout (GB300):
-//  * a CTA = 4 warps; each thread owns S sources (z_n duplicated into both
+//  * a CTA = 8 warps (S = 4) or 4 warps; each thread owns S sources (z_n duplicated into both
 //    halves of an FP32x2 register) and 11 FP32x2 accumulators per source;
 //  * the two halves of every packed register belong to two consecutive
 //    targets, so every operation of the pair update is one packed
@@ -35,7 +35,13 @@ namespace lsg {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kNW = 4;  // warps per CTA of the hot kernel
+// warps per CTA of the hot kernel: with 4 sources per thread (240 registers) one
+// 8-warp CTA per SM shares each tile among 1024 sources; narrower variants run
+// several 4-warp CTAs per SM
+template <int S>
+__host__ __device__ constexpr int warps_for() { return S >= 4 ? 8 : 4; }
+template <int S>
+__host__ __device__ constexpr int min_ctas_for() { return S >= 4 ? 1 : 3; }
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -180,12 +186,12 @@ __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc&
 }
 
 template <int S>
-__global__ void __launch_bounds__(kNW * 32, (S >= 4 ? 2 : 3))
+__global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec,
                  const EmState* __restrict__ st, const float* __restrict__ kap_n,
                  float* __restrict__ part, const int* __restrict__ table, int* __restrict__ status,
                  int num_tiles, long long units, int seg_cap) {
-  constexpr int SB = kNW * 32 * S;
+  constexpr int SB = warps_for<S>() * 32 * S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tiles = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kStages * kTileBytes);
@@ -479,8 +485,8 @@ __global__ void final_reduce_kernel(const double* __restrict__ rows, int nrows, 
 template <int S>
 cudaError_t launch_estep_t(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
                            const float* kap_n, float* part, const int* table, int* status, cudaStream_t s) {
-  estep_kernel<S><<<p.grid, kNW * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, table, status,
-                                                        p.num_tiles, p.units, p.seg_cap);
+  estep_kernel<S><<<p.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, table, status,
+                                                                   p.num_tiles, p.units, p.seg_cap);
   return cudaGetLastError();
 }
 
@@ -488,9 +494,12 @@ int resident_ctas(int S) {
   int occ = 1;
   const size_t smem = kStages * kTileBytes + kStages * sizeof(uint64_t);
   cudaError_t e = cudaSuccess;
-  if (S == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4>, kNW * 32, smem);
-  else if (S == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2>, kNW * 32, smem);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1>, kNW * 32, smem);
+  if (S == 4)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4>, warps_for<4>() * 32, smem);
+  else if (S == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2>, warps_for<2>() * 32, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1>, warps_for<1>() * 32, smem);
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -500,9 +509,10 @@ int resident_ctas(int S) {
 
 }  // namespace
 
+int warps_of(int S) { return S >= 4 ? warps_for<4>() : (S == 2 ? warps_for<2>() : warps_for<1>()); }
+
 EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
   EstepPlan p{};
-  p.NW = kNW;
   p.num_tiles = static_cast<int>((M + kTile - 1) / kTile);
   p.smem_bytes = kStages * kTileBytes + kStages * sizeof(uint64_t);
   int chosen = 1;
@@ -511,7 +521,7 @@ EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
   } else {
     const int cands[3] = {4, 2, 1};
     for (int c : cands) {
-      const int SB = kNW * 32 * c;
+      const int SB = warps_of(c) * 32 * c;
       const long long blocks = (N + SB - 1) / SB;
       const long long units = blocks * p.num_tiles;
       if (units >= 4LL * num_sms * resident_ctas(c)) {
@@ -521,7 +531,8 @@ EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
     }
   }
   p.S = chosen;
-  p.SB = kNW * 32 * chosen;
+  p.NW = warps_of(chosen);
+  p.SB = p.NW * 32 * chosen;
   p.num_blocks = static_cast<int>((N + p.SB - 1) / p.SB);
   p.units = static_cast<long long>(p.num_blocks) * p.num_tiles;
   const long long slots = static_cast<long long>(num_sms) * resident_ctas(chosen);
