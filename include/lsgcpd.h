@@ -177,6 +177,33 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const 
                               const lsgcpd_params* p, lsgcpd_result* out, double* trace,
                               void* stream);
 
+/* Largest num_pairs of lsgcpd_register_batch. */
+#define LSGCPD_MAX_PAIRS 65535
+
+/* Many independent registrations (Sec. 3, applied to each pair on its own)
+ * in one pass: every stage runs once over the whole batch, the E step as one
+ * persistent launch whose work units (source block x target tile) are split
+ * evenly over the SMs whatever the pair sizes, so that small and uneven pairs
+ * still fill the GPU.  Pair i has sources X[n_off[i] .. n_off[i+1]) and
+ * targets Y[m_off[i] .. m_off[i+1]) (rows of 3 floats, HOST or DEVICE
+ * pointers); n_off / m_off (host, num_pairs + 1 entries, n_off[0] = m_off[0]
+ * = 0, strictly increasing) give the offsets.  Each pair gets exactly the
+ * computation lsgcpd_register would give it alone (its own centring, kNN
+ * among its own targets, sigma^2_0, V, floor and convergence test); p is
+ * shared and p->knn_k must not exceed any M_i.  The shift mode (fixed or
+ * per-source) is chosen once for the batch: fixed only where it is safe for
+ * every pair.  Outputs (host): R_out (num_pairs x 9, row-major), t_out
+ * (num_pairs x 3), sigma2_out and iters_out (num_pairs each, may be NULL),
+ * trace (num_pairs x max_iters x LSGCPD_TRACE_WIDTH, may be NULL).  Returns
+ * EINVAL for an empty pair, bad offsets or num_pairs outside
+ * [1, LSGCPD_MAX_PAIRS]; ENUMERIC if the posterior mass of any pair vanished
+ * (every pair's result is still written). */
+lsgcpd_status lsgcpd_register_batch(lsgcpd_ctx* ctx, int32_t num_pairs, const float* X,
+                                    const int64_t* n_off, const float* Y, const int64_t* m_off,
+                                    const lsgcpd_params* p, double* R_out, double* t_out,
+                                    double* sigma2_out, int32_t* iters_out, double* trace,
+                                    void* stream);
+
 /* Size limits and scratch size of lsgcpd_estep_noalloc. */
 #define LSGCPD_NOALLOC_MAX_N 4096
 #define LSGCPD_NOALLOC_MAX_M 4096

@@ -77,6 +77,9 @@ def lib():
         L.lsgcpd_mstep.restype = C.c_int
         L.lsgcpd_register.argtypes = [vp, fp, i64, fp, i64, C.POINTER(Params), C.POINTER(Result), dp, vp]
         L.lsgcpd_register.restype = C.c_int
+        L.lsgcpd_register_batch.argtypes = [vp, C.c_int32, fp, C.POINTER(i64), fp, C.POINTER(i64),
+                                            C.POINTER(Params), dp, dp, dp, C.POINTER(C.c_int32), dp, vp]
+        L.lsgcpd_register_batch.restype = C.c_int
         L.lsgcpd_estep_noalloc.argtypes = [fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
                                            C.c_double, dp, fp, vp]
         L.lsgcpd_estep_noalloc.restype = C.c_int
@@ -258,6 +261,34 @@ def lsgcpd_register(ctx, X, Y, params, trace=False, stream=None):
     return out
 
 
+def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=None):
+    """Register every pair i: X[n_off[i]:n_off[i+1]] onto Y[m_off[i]:m_off[i+1]]."""
+    xp, _N, _xk = _any_ptr(X, "X")
+    yp, _M, _yk = _any_ptr(Y, "Y")
+    no = np.ascontiguousarray(np.asarray(n_off, dtype=np.int64))
+    mo = np.ascontiguousarray(np.asarray(m_off, dtype=np.int64))
+    P = no.size - 1
+    if P < 1 or mo.size != P + 1:
+        raise ValueError("n_off and m_off need num_pairs + 1 entries each")
+    if no[-1] != _N or mo[-1] != _M:
+        raise ValueError("the last offsets must equal the row counts of X and Y")
+    R = np.zeros((P, 3, 3))
+    t = np.zeros((P, 3))
+    s2 = np.zeros(P)
+    it = np.zeros(P, dtype=np.int32)
+    tr = np.zeros((P, max(params.max_iters, 1), TRACE_WIDTH)) if trace else None
+    dptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    rc = lib().lsgcpd_register_batch(ctx, P, xp, no.ctypes.data_as(C.POINTER(C.c_int64)), yp,
+                                     mo.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(params), dptr(R),
+                                     dptr(t), dptr(s2), it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     dptr(tr) if tr is not None else None, _stream(stream))
+    _check(ctx, rc)
+    out = dict(R=R, t=t, sigma2=s2, iters=it)
+    if tr is not None:
+        out["trace"] = tr
+    return out
+
+
 def lsgcpd_set_timing(ctx, enable):
     lib().lsgcpd_set_timing(ctx, 1 if enable else 0)
 
@@ -297,6 +328,9 @@ class Context:
 
     def register(self, X, Y, params, trace=False, stream=None):
         return lsgcpd_register(self.handle, X, Y, params, trace, stream)
+
+    def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None):
+        return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream)
 
     def set_timing(self, enable):
         lsgcpd_set_timing(self.handle, enable)

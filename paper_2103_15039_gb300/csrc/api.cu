@@ -1,11 +1,13 @@
 // C ABI of liblsgcpd (declared in include/lsgcpd.h): context, argument
-// validation, scratch memory, the CUDA-graph-captured EM loop and the
-// conversions between the centred working frame and the caller's frame.
+// validation, scratch memory, the batch plan, the CUDA-graph-captured EM loop
+// and the conversions between the centred working frame and the caller's frame.
+// A single registration is a batch of one pair.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 #include "lsgcpd.h"
@@ -16,18 +18,23 @@ namespace {
 
 constexpr int kMaxK = 32;
 
-struct GraphKey {
-  int64_t N = -1, M = -1;
-  int iters = -1, mode = -1, S = -1, timing = -1;
-  bool operator==(const GraphKey& o) const {
-    return N == o.N && M == o.M && iters == o.iters && mode == o.mode && S == o.S && timing == o.timing;
-  }
-};
-
 template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t cap = 0;  // elements
+};
+
+// Identity of a captured EM graph: the sizes of every pair, the shift mode, the
+// iteration count, what the graph records and the parameters its kernels take
+// by value.
+struct GraphKey {
+  std::vector<long long> sizes;
+  std::vector<unsigned char> params;
+  int iters = -1, mode = -1, S = -1, timing = -1, trace = -1;
+  bool operator==(const GraphKey& o) const {
+    return sizes == o.sizes && params == o.params && iters == o.iters && mode == o.mode && S == o.S &&
+           timing == o.timing && trace == o.trace;
+  }
 };
 
 }  // namespace
@@ -40,10 +47,12 @@ struct lsgcpd_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevBuf<float> X_in, Y_in, rec, part, knn_d, kap_n, gam_n;
   DevBuf<float4> xs, y4;
-  DevBuf<int> knn_i, knn_idx, segtab;
-  DevBuf<double> rows, red, trace, io;
-  EmState* st = nullptr;
+  DevBuf<int> knn_i, knn_idx, tab;
+  DevBuf<long long> off64;
+  DevBuf<double> rows, red, trace, io, mom;
+  DevBuf<EmState> st;
   int* status = nullptr;
+  int* done_count = nullptr;
   // graph of the EM loop
   cudaGraphExec_t gexec = nullptr;
   GraphKey gkey;
@@ -52,7 +61,7 @@ struct lsgcpd_ctx {
   cudaEvent_t t_begin = nullptr, t_prep = nullptr, t_end = nullptr;
   cudaEvent_t* t_iter = nullptr;  // 4 per iteration
   int t_iter_cap = 0;
-  double last_timing[6] = {0, 0, 0, 0, 0, 0};
+  double last_timing[5] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   int64_t h2d_bytes = 0, d2h_bytes = 0;
 };
@@ -70,9 +79,9 @@ lsgcpd_status cuda_fail(lsgcpd_ctx* c, cudaError_t e, const char* where) {
   return fail(c, LSGCPD_ECUDA, m);
 }
 
-#define LSG_CUDA(call, where)                       \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
+#define LSG_CUDA(call, where)                              \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
   } while (0)
 
@@ -96,7 +105,8 @@ lsgcpd_status check_params(lsgcpd_ctx* c, const lsgcpd_params* p) {
   if (!is_finite_d(p->alpha_max) || p->alpha_max < 0.0) return fail(c, LSGCPD_EINVAL, "alpha_max must be finite and >= 0");
   if (!is_finite_d(p->lambda) || p->lambda < 0.0) return fail(c, LSGCPD_EINVAL, "lambda must be finite and >= 0");
   if (!is_finite_d(p->tol) || p->tol < 0.0) return fail(c, LSGCPD_EINVAL, "tol must be finite and >= 0");
-  if (!is_finite_d(p->volume) || !is_finite_d(p->sigma2_init)) return fail(c, LSGCPD_EINVAL, "volume/sigma2_init must be finite");
+  if (!is_finite_d(p->volume) || !is_finite_d(p->sigma2_init))
+    return fail(c, LSGCPD_EINVAL, "volume/sigma2_init must be finite");
   for (int i = 0; i < 9; ++i)
     if (!is_finite_d(p->init_R[i])) return fail(c, LSGCPD_EINVAL, "init_R must be finite");
   for (int i = 0; i < 3; ++i)
@@ -177,48 +187,65 @@ cudaError_t leave(lsgcpd_ctx* c, void* stream) {
   return cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), c->ev_out, 0);
 }
 
-// Scratch sizes for a problem (N, M, k) with plan p.
-lsgcpd_status reserve(lsgcpd_ctx* c, int64_t N, int64_t M, int k, const EstepPlan& p, int iters,
-                      bool host_inputs) {
-  const size_t n_pad = static_cast<size_t>(p.num_blocks) * p.SB;
-  const size_t m_pad = static_cast<size_t>(p.num_tiles) * kTile;
-  const int splits = knn_splits(M, c->num_sms);
-  bool grew = false;
-  auto grow = [&](auto& buf, size_t n) -> cudaError_t {
-    if (buf.cap >= (n ? n : 1)) return cudaSuccess;
+// Scratch for a plan; k = 0 skips the neighbour buffers.  A buffer that has to
+// grow moves, so the captured graph (which holds the old addresses) is dropped.
+lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool host_inputs) {
+  const Geo& g = p.g;
+  const size_t n_pad = static_cast<size_t>(g.B) * g.SB;
+  const size_t m_pad = static_cast<size_t>(g.T) * kTile;
+  const long long Ntot = p.off64[g.P], Mtot = p.off64[2 * g.P + 1];
+  const int chunks = stats_chunks(g);
+  bool grew = false, ok = true;
+  auto grow = [&](auto& buf, size_t n) {
+    if (!ok || buf.cap >= (n ? n : 1)) return;
     grew = true;
-    return ensure(buf, n);
+    ok = ensure(buf, n) == cudaSuccess;
   };
-  cudaError_t e = cudaSuccess;
-  if (grow(c->xs, n_pad) != cudaSuccess || grow(c->rec, m_pad * kPlanes) != cudaSuccess ||
-      grow(c->part, estep_partial_floats(p)) != cudaSuccess ||
-      grow(c->rows, static_cast<size_t>(combine_rows(N, c->num_sms)) * kGlob) != cudaSuccess ||
-      grow(c->segtab, p.table.size()) != cudaSuccess ||
-      grow(c->kap_n, n_pad) != cudaSuccess || grow(c->gam_n, n_pad) != cudaSuccess ||
-      grow(c->trace, static_cast<size_t>(iters > 0 ? iters : 1) * LSGCPD_TRACE_WIDTH) != cudaSuccess)
-    e = cudaErrorMemoryAllocation;
-  if (e == cudaSuccess && k > 0) {
-    if (grow(c->y4, static_cast<size_t>(M)) != cudaSuccess ||
-        grow(c->knn_d, static_cast<size_t>(splits) * M * k) != cudaSuccess ||
-        grow(c->knn_i, static_cast<size_t>(splits) * M * k) != cudaSuccess ||
-        grow(c->knn_idx, static_cast<size_t>(M) * k) != cudaSuccess)
-      e = cudaErrorMemoryAllocation;
+  grow(c->xs, n_pad);
+  grow(c->rec, m_pad * kPlanes);
+  grow(c->part, estep_partial_floats(g));
+  grow(c->rows, static_cast<size_t>(g.combine_ctas) * kGlob);
+  grow(c->kap_n, n_pad);
+  grow(c->gam_n, n_pad);
+  grow(c->tab, p.tab.size());
+  grow(c->off64, p.off64.size());
+  grow(c->st, static_cast<size_t>(g.P));
+  grow(c->mom, static_cast<size_t>(g.P) * kGlob);
+  grow(c->red, static_cast<size_t>(g.P) * chunks * 20);
+  grow(c->trace, static_cast<size_t>(g.P) * (iters > 0 ? iters : 1) * LSGCPD_TRACE_WIDTH);
+  if (k > 0) {
+    const int splits = knn_splits(g, c->num_sms);
+    grow(c->y4, static_cast<size_t>(Mtot));
+    grow(c->knn_d, static_cast<size_t>(splits) * Mtot * k);
+    grow(c->knn_i, static_cast<size_t>(splits) * Mtot * k);
+    grow(c->knn_idx, static_cast<size_t>(Mtot) * k);
   }
-  if (e == cudaSuccess && host_inputs) {
-    if (grow(c->X_in, static_cast<size_t>(N) * 3) != cudaSuccess ||
-        grow(c->Y_in, static_cast<size_t>(M) * 3) != cudaSuccess)
-      e = cudaErrorMemoryAllocation;
+  if (host_inputs) {
+    grow(c->X_in, static_cast<size_t>(Ntot) * 3);
+    grow(c->Y_in, static_cast<size_t>(Mtot) * 3);
   }
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, LSGCPD_ENOMEM, "device allocation failed");
-  }
-  if (grew && c->gexec) {  // buffers moved: the captured graph is stale
+  if (grew && c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     c->gkey = GraphKey();
   }
+  if (!ok) {
+    cudaGetLastError();
+    return fail(c, LSGCPD_ENOMEM, "device allocation failed");
+  }
   return LSGCPD_OK;
+}
+
+Dev dev_of(lsgcpd_ctx* c) { return Dev{c->tab.p, c->off64.p, c->st.p, c->done_count}; }
+
+// The plan's tables, and the words that must start at zero, for this call.
+cudaError_t upload_plan(lsgcpd_ctx* c, const BatchPlan& p, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(c->tab.p, p.tab.data(), sizeof(int) * p.tab.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->off64.p, p.off64.data(), sizeof(long long) * p.off64.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->done_count, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  return e;
 }
 
 cudaError_t ensure_iter_events(lsgcpd_ctx* c, int iters) {
@@ -274,6 +301,163 @@ void moments_to_raw(const double* mc, const double mu[3], double* mr) {
   }
 }
 
+// One or more registrations: X and Y are the concatenated clouds (host or
+// device), sizes N[i], M[i].  Results per pair in the caller's frame.
+lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N,
+                               const std::vector<long long>& M, const lsgcpd_params* p, double* R_out, double* t_out,
+                               double* sigma2_out, int32_t* iters_out, int32_t* mode_out, double* trace,
+                               void* stream) {
+  const int P = static_cast<int>(N.size());
+  const int k = p->knn_k;
+  for (int i = 0; i < P; ++i)
+    if (k > M[i]) return fail(c, LSGCPD_EINVAL, "knn_k must not exceed the target count of any pair");
+  LSG_CUDA(enter(c, stream), "stream");
+  const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
+  const BatchPlan plan = plan_batch(N, M, c->num_sms, 0);
+  const Geo& g = plan.g;
+  const long long Ntot = plan.off64[P], Mtot = plan.off64[2 * P + 1];
+  const int iters = p->max_iters;
+  lsgcpd_status rs = reserve(c, plan, k, iters, !xd || !yd);
+  if (rs != LSGCPD_OK) return rs;
+  cudaStream_t s = c->stream;
+  const Dev d = dev_of(c);
+  if (c->timing) {
+    LSG_CUDA(ensure_iter_events(c, iters > 0 ? iters : 1), "events");
+    LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
+  }
+  const float* Xd = X;
+  const float* Yd = Y;
+  if (!xd) {
+    LSG_CUDA(cudaMemcpyAsync(c->X_in.p, X, sizeof(float) * 3 * Ntot, cudaMemcpyHostToDevice, s), "copy X");
+    Xd = c->X_in.p;
+  }
+  if (!yd) {
+    LSG_CUDA(cudaMemcpyAsync(c->Y_in.p, Y, sizeof(float) * 3 * Mtot, cudaMemcpyHostToDevice, s), "copy Y");
+    Yd = c->Y_in.p;
+  }
+  LSG_CUDA(upload_plan(c, plan, s), "plan");
+  int64_t launches = 0;
+  LSG_CUDA(check_finite(Xd, Ntot * 3, c->status, s), "check");
+  LSG_CUDA(check_finite(Yd, Mtot * 3, c->status, s), "check");
+  const DevParams dp = dev_params(p);
+  LSG_CUDA(launch_init(plan, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
+  const int splits = knn_splits(g, c->num_sms);
+  LSG_CUDA(launch_knn(plan, d, Yd, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, s), "knn");
+  LSG_CUDA(launch_geometry(plan, d, Yd, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
+                           nullptr, nullptr, nullptr, s),
+           "geometry");
+  launches += 2 + 4 + 3 + 1;
+  if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
+  std::vector<EmState> hs(P);
+  int status = 0;
+  LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaStreamSynchronize(s), "sync");
+  if (status & 8) {
+    leave(c, stream);
+    return fail(c, LSGCPD_EINVAL, "inputs contain NaN or Inf");
+  }
+  // one shift mode for the whole batch: fixed shift only if it is safe for every pair
+  const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
+  int mode = 0;
+  for (int i = 0; i < P; ++i) mode |= choose_mode(p->w, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
+  if (iters > 0) {
+    GraphKey key;
+    key.sizes = N;
+    key.sizes.insert(key.sizes.end(), M.begin(), M.end());
+    key.params.assign(reinterpret_cast<const unsigned char*>(&dp),
+                      reinterpret_cast<const unsigned char*>(&dp) + sizeof(dp));
+    key.iters = iters;
+    key.mode = mode;
+    key.S = g.S;
+    key.timing = c->timing;
+    key.trace = trace ? 1 : 0;
+    if (!(c->gexec && key == c->gkey)) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      cudaGraph_t gr = nullptr;
+      LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+      cudaError_t ce = cudaSuccess;
+      for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
+        if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
+        if (ce == cudaSuccess && mode == 1) ce = launch_shift(plan, d, c->xs.p, c->rec.p, c->kap_n.p, c->gam_n.p, s);
+        if (ce == cudaSuccess)
+          ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode ? c->kap_n.p : nullptr, c->part.p, c->status, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
+        if (ce == cudaSuccess)
+          ce = launch_combine(plan, d, c->xs.p, c->part.p, mode ? c->kap_n.p : nullptr, mode ? c->gam_n.p : nullptr,
+                              c->rows.p, nullptr, s);
+        if (ce == cudaSuccess) ce = launch_final_reduce(plan, d, c->rows.p, c->mom.p, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
+        if (ce == cudaSuccess) ce = launch_mstep(plan, d, c->mom.p, dp, trace ? c->trace.p : nullptr, iters, s);
+        if (ce == cudaSuccess && c->timing)
+          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
+      }
+      cudaError_t ee = cudaStreamEndCapture(s, &gr);
+      if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return cuda_fail(c, ce != cudaSuccess ? ce : ee, "graph capture");
+      }
+      cudaError_t ie = cudaGraphInstantiate(&c->gexec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, ie, "graph instantiate");
+      }
+      c->gkey = key;
+    }
+    LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
+    launches += static_cast<int64_t>(iters) * (mode ? 5 : 4);
+  }
+  if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
+  LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  if (trace && iters > 0)
+    LSG_CUDA(cudaMemcpyAsync(trace, c->trace.p, sizeof(double) * LSGCPD_TRACE_WIDTH * iters * P,
+                             cudaMemcpyDeviceToHost, s),
+             "copy trace");
+  LSG_CUDA(cudaStreamSynchronize(s), "sync");
+  LSG_CUDA(leave(c, stream), "stream");
+  c->launches = launches;
+  c->h2d_bytes = (xd ? 0 : 12 * Ntot) + (yd ? 0 : 12 * Mtot) +
+                 static_cast<int64_t>(sizeof(int) * plan.tab.size() + sizeof(long long) * plan.off64.size());
+  c->d2h_bytes = 2 * static_cast<int64_t>(sizeof(EmState) * P + sizeof(int)) +
+                 (trace && iters > 0 ? static_cast<int64_t>(sizeof(double)) * LSGCPD_TRACE_WIDTH * iters * P : 0);
+  bool numeric = false;
+  for (int i = 0; i < P; ++i) {
+    const EmState& h = hs[i];
+    // result in the caller's frame: t = t_c + mu_y - R mu_x
+    for (int q = 0; q < 9; ++q) R_out[9 * i + q] = h.R[q];
+    for (int q = 0; q < 3; ++q)
+      t_out[3 * i + q] =
+          h.t[q] + h.mu_y[q] - (h.R[3 * q] * h.mu_x[0] + h.R[3 * q + 1] * h.mu_x[1] + h.R[3 * q + 2] * h.mu_x[2]);
+    if (sigma2_out) sigma2_out[i] = h.sigma2;
+    if (iters_out) iters_out[i] = h.iter;
+    numeric = numeric || h.numeric_fail;
+  }
+  if (mode_out) *mode_out = mode;
+  if (c->timing) {
+    double es = 0, cb = 0, ms = 0;
+    for (int it = 0; it < iters; ++it) {
+      es += elapsed_ms(c->t_iter[4 * it], c->t_iter[4 * it + 1]);
+      cb += elapsed_ms(c->t_iter[4 * it + 1], c->t_iter[4 * it + 2]);
+      ms += elapsed_ms(c->t_iter[4 * it + 2], c->t_iter[4 * it + 3]);
+    }
+    c->last_timing[0] = elapsed_ms(c->t_begin, c->t_end);
+    c->last_timing[1] = es;
+    c->last_timing[2] = cb;
+    c->last_timing[3] = ms;
+    c->last_timing[4] = elapsed_ms(c->t_begin, c->t_prep);
+  }
+  if (status & kStatusTimeout) return fail(c, LSGCPD_ETIMEOUT, "E-step tile wait timed out");
+  if (numeric) return fail(c, LSGCPD_ENUMERIC, "posterior mass vanished (N_P = 0)");
+  return LSGCPD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -318,15 +502,15 @@ lsgcpd_status lsgcpd_create(lsgcpd_ctx** out, int device, int64_t max_N, int64_t
     cudaGetLastError();
     return bail(LSGCPD_ECUDA);
   }
-  if (cudaMalloc(&c->st, sizeof(EmState)) != cudaSuccess || cudaMalloc(&c->status, sizeof(int)) != cudaSuccess ||
-      ensure(c->red, 1024 * 20) != cudaSuccess || ensure(c->io, 128) != cudaSuccess) {
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->done_count, sizeof(int)) != cudaSuccess ||
+      ensure(c->io, 128) != cudaSuccess) {
     cudaGetLastError();
     return bail(LSGCPD_ENOMEM);
   }
-  cudaMemset(c->st, 0, sizeof(EmState));
   cudaMemset(c->status, 0, sizeof(int));
-  const EstepPlan p = plan_estep(max_N, max_M, c->num_sms, 0);
-  if (reserve(c, max_N, max_M, 10, p, 50, false) != LSGCPD_OK) return bail(LSGCPD_ENOMEM);
+  cudaMemset(c->done_count, 0, sizeof(int));
+  const BatchPlan p = plan_batch({max_N}, {max_M}, c->num_sms, 0);
+  if (reserve(c, p, 10, 50, false) != LSGCPD_OK) return bail(LSGCPD_ENOMEM);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     return bail(LSGCPD_ECUDA);
@@ -340,19 +524,11 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  float* fb[] = {c->X_in.p, c->Y_in.p, c->rec.p, c->part.p, c->knn_d.p, c->kap_n.p, c->gam_n.p};
-  for (float* p : fb)
-    if (p) cudaFree(p);
-  if (c->xs.p) cudaFree(c->xs.p);
-  if (c->y4.p) cudaFree(c->y4.p);
-  if (c->knn_i.p) cudaFree(c->knn_i.p);
-  if (c->knn_idx.p) cudaFree(c->knn_idx.p);
-  if (c->segtab.p) cudaFree(c->segtab.p);
-  double* db[] = {c->rows.p, c->red.p, c->trace.p, c->io.p};
-  for (double* p : db)
-    if (p) cudaFree(p);
-  if (c->st) cudaFree(c->st);
-  if (c->status) cudaFree(c->status);
+  void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->kap_n.p, c->gam_n.p,
+                  c->xs.p,   c->y4.p,      c->knn_i.p, c->knn_idx.p, c->tab.p, c->off64.p, c->rows.p,
+                  c->red.p,  c->trace.p,   c->io.p,  c->mom.p,   c->st.p,    c->status,  c->done_count};
+  for (void* q : bufs)
+    if (q) cudaFree(q);
   if (c->t_iter) {
     for (int i = 0; i < 4 * c->t_iter_cap; ++i) cudaEventDestroy(c->t_iter[i]);
     delete[] c->t_iter;
@@ -382,8 +558,8 @@ lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* c, double out[8]) {
   return c->timing ? LSGCPD_OK : LSGCPD_EINVAL;
 }
 
-lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const lsgcpd_params* p,
-                                float* normals, float* kappa, float* alpha, int32_t* knn_idx, void* stream) {
+lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const lsgcpd_params* p, float* normals,
+                                float* kappa, float* alpha, int32_t* knn_idx, void* stream) {
   if (!c) return LSGCPD_EINVAL;
   c->err.clear();
   if (!Y || M < 1) return fail(c, LSGCPD_EINVAL, "Y must be non-NULL with M >= 1");
@@ -392,20 +568,21 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   const int k = p->knn_k;
   if (k < 1 || k > kMaxK || k > M) return fail(c, LSGCPD_EINVAL, "knn_k must satisfy 1 <= k <= min(M, 32)");
   LSG_CUDA(enter(c, stream), "stream");
-  const EstepPlan plan = plan_estep(M, M, c->num_sms, 1);
-  lsgcpd_status rs = reserve(c, M, M, k, plan, 1, false);
+  // a batch of one whose source cloud is Y itself (only the target side is used)
+  const BatchPlan plan = plan_batch({M}, {M}, c->num_sms, 1);
+  lsgcpd_status rs = reserve(c, plan, k, 1, false);
   if (rs != LSGCPD_OK) return rs;
   cudaStream_t s = c->stream;
-  c->launches = 0;
-  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
+  const Dev d = dev_of(c);
+  LSG_CUDA(upload_plan(c, plan, s), "plan");
   LSG_CUDA(check_finite(Y, M * 3, c->status, s), "check");
-  const int64_t n_pad = static_cast<int64_t>(plan.num_blocks) * plan.SB;
-  LSG_CUDA(launch_center_only(Y, M, Y, M, c->red.p, c->st, c->xs.p, n_pad, s), "center");
-  const int splits = knn_splits(M, c->num_sms);
+  const DevParams dp = dev_params(p);
+  LSG_CUDA(launch_init(plan, d, Y, Y, dp, false, c->red.p, c->xs.p, s), "center");
+  const int splits = knn_splits(plan.g, c->num_sms);
   int* idx = knn_idx ? knn_idx : c->knn_idx.p;
-  LSG_CUDA(launch_knn(Y, M, k, c->y4.p, c->knn_d.p, c->knn_i.p, idx, splits, s), "knn");
-  LSG_CUDA(launch_geometry(Y, M, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->st, c->rec.p,
-                           plan.num_tiles, normals, kappa, alpha, s),
+  LSG_CUDA(launch_knn(plan, d, Y, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, idx, s), "knn");
+  LSG_CUDA(launch_geometry(plan, d, Y, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p, normals,
+                           kappa, alpha, s),
            "geometry");
   c->launches = 7;
   int status = 0;
@@ -417,9 +594,8 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
 }
 
 lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float* Y, const float* normals,
-                           const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9],
-                           const double t[3], double sigma2, double volume, double* moments, float* per_n,
-                           void* stream) {
+                           const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9], const double t[3],
+                           double sigma2, double volume, double* moments, float* per_n, void* stream) {
   if (!c) return LSGCPD_EINVAL;
   c->err.clear();
   if (!X || !Y || !normals || !alpha || !R || !t) return fail(c, LSGCPD_EINVAL, "NULL input");
@@ -433,45 +609,40 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   for (int i = 0; i < 3; ++i)
     if (!is_finite_d(t[i])) return fail(c, LSGCPD_EINVAL, "t must be finite");
   LSG_CUDA(enter(c, stream), "stream");
-  const EstepPlan plan = plan_estep(N, M, c->num_sms, 0);
-  lsgcpd_status rs = reserve(c, N, M, 0, plan, 1, false);
+  const BatchPlan plan = plan_batch({N}, {M}, c->num_sms, 0);
+  lsgcpd_status rs = reserve(c, plan, 0, 1, false);
   if (rs != LSGCPD_OK) return rs;
   cudaStream_t s = c->stream;
-  const int64_t n_pad = static_cast<int64_t>(plan.num_blocks) * plan.SB;
-  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
+  const Dev d = dev_of(c);
+  LSG_CUDA(upload_plan(c, plan, s), "plan");
   LSG_CUDA(check_finite(X, N * 3, c->status, s), "check");
   LSG_CUDA(check_finite(Y, M * 3, c->status, s), "check");
   LSG_CUDA(check_finite(normals, M * 3, c->status, s), "check");
   LSG_CUDA(check_finite(alpha, M, c->status, s), "check");
-  LSG_CUDA(launch_center_only(X, N, Y, M, c->red.p, c->st, c->xs.p, n_pad, s), "center");
-  LSG_CUDA(launch_estep_constants(c->st, sigma2, p->w, volume, R, t, s), "constants");
-  LSG_CUDA(launch_pack(Y, normals, alpha, M, p->include_alpha_norm, c->st, c->rec.p, plan.num_tiles, s), "pack");
+  const DevParams dp = dev_params(p);
+  LSG_CUDA(launch_init(plan, d, X, Y, dp, false, c->red.p, c->xs.p, s), "center");
+  LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
+  LSG_CUDA(launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c->rec.p, s), "pack");
   const int mode = choose_mode(p->w, sigma2, volume, M, p->include_alpha_norm ? 12.0 : 0.0);
-  int64_t launches = 11;
-  LSG_CUDA(cudaMemcpyAsync(c->segtab.p, plan.table.data(), sizeof(int) * plan.table.size(),
-                           cudaMemcpyHostToDevice, s),
-           "table");
-  const int nrows = combine_rows(N, c->num_sms);
+  int64_t launches = 9;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   if (mode == 1) {
-    LSG_CUDA(launch_shift(plan, c->xs.p, c->rec.p, c->st, N, c->kap_n.p, c->gam_n.p, s), "shift");
+    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, c->kap_n.p, c->gam_n.p, s), "shift");
     ++launches;
   }
-  LSG_CUDA(launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p, c->segtab.p,
-                        c->status, s),
-           "estep");
+  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode ? c->kap_n.p : nullptr, c->part.p, c->status, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  LSG_CUDA(launch_combine(plan, c->xs.p, N, c->part.p, c->segtab.p, c->st, mode ? c->kap_n.p : nullptr,
-                          mode ? c->gam_n.p : nullptr, c->rows.p, nrows, per_n, s),
+  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode ? c->kap_n.p : nullptr, mode ? c->gam_n.p : nullptr,
+                          c->rows.p, per_n, s),
            "combine");
-  LSG_CUDA(launch_final_reduce(c->rows.p, nrows, c->io.p, nullptr, s), "reduce");
+  LSG_CUDA(launch_final_reduce(plan, d, c->rows.p, c->mom.p, s), "reduce");
   launches += 3;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   double mom[LSGCPD_MOMENTS];
   EmState hs;
   int status = 0;
-  LSG_CUDA(cudaMemcpyAsync(mom, c->io.p, sizeof(mom), cudaMemcpyDeviceToHost, s), "copy");
-  LSG_CUDA(cudaMemcpyAsync(&hs, c->st, sizeof(EmState), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(mom, c->mom.p, sizeof(mom), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(&hs, c->st.p, sizeof(EmState), cudaMemcpyDeviceToHost, s), "copy");
   LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
   LSG_CUDA(leave(c, stream), "stream");
@@ -492,8 +663,8 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
 }
 
 lsgcpd_status lsgcpd_mstep(lsgcpd_ctx* c, const double* moments, const double R[9], const double t[3],
-                           const lsgcpd_params* p, double R_out[9], double t_out[3], double* sigma2_out,
-                           int32_t* info, void* stream) {
+                           const lsgcpd_params* p, double R_out[9], double t_out[3], double* sigma2_out, int32_t* info,
+                           void* stream) {
   if (!c) return LSGCPD_EINVAL;
   c->err.clear();
   if (!moments || !R || !t || !R_out || !t_out) return fail(c, LSGCPD_EINVAL, "NULL argument");
@@ -539,149 +710,37 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* c, const float* X, int64_t N, const fl
   if (ps != LSGCPD_OK) return ps;
   const int k = p->knn_k;
   if (k < 1 || k > kMaxK || k > M) return fail(c, LSGCPD_EINVAL, "knn_k must satisfy 1 <= k <= min(M, 32)");
-  LSG_CUDA(enter(c, stream), "stream");
-  const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
-  const EstepPlan plan = plan_estep(N, M, c->num_sms, 0);
-  const int iters = p->max_iters;
-  lsgcpd_status rs = reserve(c, N, M, k, plan, iters, !xd || !yd);
-  if (rs != LSGCPD_OK) return rs;
-  cudaStream_t s = c->stream;
-  if (c->timing) {
-    LSG_CUDA(ensure_iter_events(c, iters > 0 ? iters : 1), "events");
-    LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
-  }
-  const float* Xd = X;
-  const float* Yd = Y;
-  if (!xd) {
-    LSG_CUDA(cudaMemcpyAsync(c->X_in.p, X, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s), "copy X");
-    Xd = c->X_in.p;
-  }
-  if (!yd) {
-    LSG_CUDA(cudaMemcpyAsync(c->Y_in.p, Y, sizeof(float) * 3 * M, cudaMemcpyHostToDevice, s), "copy Y");
-    Yd = c->Y_in.p;
-  }
-  int64_t launches = 0;
-  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
-  LSG_CUDA(check_finite(Xd, N * 3, c->status, s), "check");
-  LSG_CUDA(check_finite(Yd, M * 3, c->status, s), "check");
-  const DevParams dp = dev_params(p);
-  const int64_t n_pad = static_cast<int64_t>(plan.num_blocks) * plan.SB;
-  LSG_CUDA(launch_init(Xd, N, Yd, M, dp, c->red.p, c->st, c->xs.p, n_pad, s), "init");
-  const int splits = knn_splits(M, c->num_sms);
-  LSG_CUDA(launch_knn(Yd, M, k, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, splits, s), "knn");
-  LSG_CUDA(launch_geometry(Yd, M, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->st,
-                           c->rec.p, plan.num_tiles, nullptr, nullptr, nullptr, s),
-           "geometry");
-  launches += 2 + 4 + 3 + 1;
-  if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  EmState hs;
-  int status = 0;
-  LSG_CUDA(cudaMemcpyAsync(&hs, c->st, sizeof(EmState), cudaMemcpyDeviceToHost, s), "copy");
-  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-  LSG_CUDA(cudaStreamSynchronize(s), "sync");
-  if (status & 8) {
-    leave(c, stream);
-    return fail(c, LSGCPD_EINVAL, "inputs contain NaN or Inf");
-  }
-  const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
-  const int mode = choose_mode(p->w, hs.sigma2_floor, hs.V, M, l_extra);
-  const int nrows = combine_rows(N, c->num_sms);
-  LSG_CUDA(cudaMemcpyAsync(c->segtab.p, plan.table.data(), sizeof(int) * plan.table.size(),
-                           cudaMemcpyHostToDevice, s),
-           "table");
-  if (iters > 0) {
-    GraphKey key;
-    key.N = N;
-    key.M = M;
-    key.iters = iters;
-    key.mode = mode;
-    key.S = plan.S;
-    key.timing = c->timing;
-    if (!(c->gexec && key == c->gkey)) {
-      if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
-      cudaGraph_t g = nullptr;
-      LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
-      cudaError_t ce = cudaSuccess;
-      for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
-        if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess && mode == 1)
-          ce = launch_shift(plan, c->xs.p, c->rec.p, c->st, N, c->kap_n.p, c->gam_n.p, s);
-        if (ce == cudaSuccess)
-          ce = launch_estep(plan, c->xs.p, c->rec.p, c->st, mode ? c->kap_n.p : nullptr, c->part.p,
-                            c->segtab.p, c->status, s);
-        if (ce == cudaSuccess && c->timing)
-          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess)
-          ce = launch_combine(plan, c->xs.p, N, c->part.p, c->segtab.p, c->st, mode ? c->kap_n.p : nullptr,
-                              mode ? c->gam_n.p : nullptr, c->rows.p, nrows, nullptr, s);
-        if (ce == cudaSuccess) ce = launch_final_reduce(c->rows.p, nrows, c->io.p, c->st, s);
-        if (ce == cudaSuccess && c->timing)
-          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess) ce = launch_mstep(c->io.p, c->st, dp, c->trace.p, s);
-        if (ce == cudaSuccess && c->timing)
-          ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
-      }
-      cudaError_t ee = cudaStreamEndCapture(s, &g);
-      if (ce != cudaSuccess || ee != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return cuda_fail(c, ce != cudaSuccess ? ce : ee, "graph capture");
-      }
-      cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (ie != cudaSuccess) {
-        c->gexec = nullptr;
-        return cuda_fail(c, ie, "graph instantiate");
-      }
-      c->gkey = key;
-    }
-    LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * (mode ? 5 : 4);
-  }
-  if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
-  LSG_CUDA(cudaMemcpyAsync(&hs, c->st, sizeof(EmState), cudaMemcpyDeviceToHost, s), "copy");
-  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
-  if (trace && iters > 0)
-    LSG_CUDA(cudaMemcpyAsync(trace, c->trace.p, sizeof(double) * LSGCPD_TRACE_WIDTH * iters,
-                             cudaMemcpyDeviceToHost, s),
-             "copy trace");
-  LSG_CUDA(cudaStreamSynchronize(s), "sync");
-  LSG_CUDA(leave(c, stream), "stream");
-  c->launches = launches;
-  c->h2d_bytes = (xd ? 0 : 12 * N) + (yd ? 0 : 12 * M) + static_cast<int64_t>(sizeof(int) * plan.table.size());
-  c->d2h_bytes = 2 * static_cast<int64_t>(sizeof(EmState) + sizeof(int)) +
-                 (trace && iters > 0 ? static_cast<int64_t>(sizeof(double)) * LSGCPD_TRACE_WIDTH * iters : 0);
-  // result in the caller's frame: t = t_c + mu_y - R mu_x
-  for (int i = 0; i < 9; ++i) out->R[i] = hs.R[i];
-  for (int i = 0; i < 3; ++i)
-    out->t[i] = hs.t[i] + hs.mu_y[i] - (hs.R[3 * i] * hs.mu_x[0] + hs.R[3 * i + 1] * hs.mu_x[1] + hs.R[3 * i + 2] * hs.mu_x[2]);
-  out->sigma2 = hs.sigma2;
-  out->iters = hs.iter;
+  double s2 = 0;
+  int32_t iters = 0, mode = 0;
+  lsgcpd_status rs = run_registration(c, X, Y, {N}, {M}, p, out->R, out->t, &s2, &iters, &mode, trace, stream);
+  out->sigma2 = s2;
+  out->iters = iters;
   out->mode = mode;
-  out->ms_estep = 0;
-  out->ms_total = 0;
-  if (c->timing) {
-    const double tot = elapsed_ms(c->t_begin, c->t_end);
-    const double prep = elapsed_ms(c->t_begin, c->t_prep);
-    double es = 0, cb = 0, ms = 0;
-    for (int it = 0; it < iters; ++it) {
-      es += elapsed_ms(c->t_iter[4 * it], c->t_iter[4 * it + 1]);
-      cb += elapsed_ms(c->t_iter[4 * it + 1], c->t_iter[4 * it + 2]);
-      ms += elapsed_ms(c->t_iter[4 * it + 2], c->t_iter[4 * it + 3]);
-    }
-    c->last_timing[0] = tot;
-    c->last_timing[1] = es;
-    c->last_timing[2] = cb;
-    c->last_timing[3] = ms;
-    c->last_timing[4] = prep;
-    out->ms_estep = es;
-    out->ms_total = tot;
+  out->ms_estep = c->timing ? c->last_timing[1] : 0.0;
+  out->ms_total = c->timing ? c->last_timing[0] : 0.0;
+  return rs;
+}
+
+lsgcpd_status lsgcpd_register_batch(lsgcpd_ctx* c, int32_t num_pairs, const float* X, const int64_t* n_off,
+                                    const float* Y, const int64_t* m_off, const lsgcpd_params* p, double* R_out,
+                                    double* t_out, double* sigma2_out, int32_t* iters_out, double* trace,
+                                    void* stream) {
+  if (!c) return LSGCPD_EINVAL;
+  c->err.clear();
+  if (num_pairs < 1 || num_pairs > LSGCPD_MAX_PAIRS) return fail(c, LSGCPD_EINVAL, "num_pairs out of range");
+  if (!X || !Y || !n_off || !m_off || !R_out || !t_out) return fail(c, LSGCPD_EINVAL, "NULL argument");
+  lsgcpd_status ps = check_params(c, p);
+  if (ps != LSGCPD_OK) return ps;
+  const int k = p->knn_k;
+  if (k < 1 || k > kMaxK) return fail(c, LSGCPD_EINVAL, "knn_k must satisfy 1 <= k <= 32");
+  if (n_off[0] != 0 || m_off[0] != 0) return fail(c, LSGCPD_EINVAL, "offsets must start at 0");
+  std::vector<long long> N(num_pairs), M(num_pairs);
+  for (int i = 0; i < num_pairs; ++i) {
+    N[i] = n_off[i + 1] - n_off[i];
+    M[i] = m_off[i + 1] - m_off[i];
+    if (N[i] < 1 || M[i] < 1) return fail(c, LSGCPD_EINVAL, "every pair needs N >= 1 and M >= 1");
   }
-  if (status & kStatusTimeout) return fail(c, LSGCPD_ETIMEOUT, "E-step tile wait timed out");
-  if (hs.numeric_fail) return fail(c, LSGCPD_ENUMERIC, "posterior mass vanished (N_P = 0)");
-  return LSGCPD_OK;
+  return run_registration(c, X, Y, N, M, p, R_out, t_out, sigma2_out, iters_out, nullptr, trace, stream);
 }
 
 }  // extern "C"

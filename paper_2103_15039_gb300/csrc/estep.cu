@@ -185,75 +185,93 @@ __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc&
   dst[10 * SB + nl] = a.d.x + a.d.y;
 }
 
+// Producer/consumer cursor over a CTA's units: (source block, unit) advancing
+// monotonically; the block of a unit is found by walking unit_off forward.
+struct Cursor {
+  int b;
+  __device__ __forceinline__ int advance(const int* unit_off, long long u) {
+    while (u >= unit_off[b + 1]) ++b;
+    return b;
+  }
+};
+
 template <int S>
 __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
-    estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec,
-                 const EmState* __restrict__ st, const float* __restrict__ kap_n,
-                 float* __restrict__ part, const int* __restrict__ table, int* __restrict__ status,
-                 int num_tiles, long long units, int seg_cap) {
+    estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
+                 const float* __restrict__ kap_n, float* __restrict__ part, const int* __restrict__ tab,
+                 const int* __restrict__ done_count, int* __restrict__ status, Geo g) {
   constexpr int SB = warps_for<S>() * 32 * S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tiles = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kStages * kTileBytes);
 
-  if (st->done) return;
+  if (*done_count >= g.P) return;
+  const int* tile_off = tab + g.o_tile_off;
+  const int* block_pair = tab + g.o_block_pair;
+  const int* unit_off = tab + g.o_unit_off;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
   const long long G = gridDim.x;
-  const long long u0 = static_cast<long long>(blockIdx.x) * units / G;
-  const long long u1 = static_cast<long long>(blockIdx.x + 1) * units / G;
+  const long long u0 = static_cast<long long>(blockIdx.x) * g.U / G;
+  const long long u1 = static_cast<long long>(blockIdx.x + 1) * g.U / G;
   const int n_units = static_cast<int>(u1 - u0);
   if (n_units <= 0) return;
+  const int first_block = tab[g.o_cta_block + blockIdx.x];
+  const int first_slot = tab[g.o_cta_slot + blockIdx.x];
 
+  Cursor prod{first_block};  // used by thread 0 only
+  auto tile_of = [&](long long u) -> long long {
+    const int b = prod.advance(unit_off, u);
+    return static_cast<long long>(tile_off[block_pair[b]]) + (u - unit_off[b]);
+  };
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < kStages && i < n_units; ++i) {
-      const long long tile = (u0 + i) % num_tiles;
-      bulk_load(tiles + i * kTileFloats, rec + tile * kTileFloats, kTileBytes, &full[i]);
-    }
+    for (int i = 0; i < kStages && i < n_units; ++i)
+      bulk_load(tiles + i * kTileFloats, rec + tile_of(u0 + i) * kTileFloats, kTileBytes, &full[i]);
   }
-
-  const float2 nc = dup(st->neg_c);
-  float Rm[9], tv[3];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Rm[i] = st->Rf[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) tv[i] = st->tf[i];
-  const float kap_uniform = st->kap;
 
   bool abort = false;
   int seg = 0;
   int i = 0;  // units consumed by this CTA
   long long u = u0;
+  Cursor cons{first_block};
   while (u < u1) {
-    const int b = static_cast<int>(u / num_tiles);
-    const long long block_end = static_cast<long long>(b + 1) * num_tiles;
-    long long seg_end = u + seg_cap;
+    const int b = cons.advance(unit_off, u);
+    const EmState* sp = st + block_pair[b];
+    const long long block_end = unit_off[b + 1];
+    long long seg_end = u + g.seg_cap;
     if (seg_end > block_end) seg_end = block_end;
     if (seg_end > u1) seg_end = u1;
 
+    const float2 nc = dup(sp->neg_c);
+    float Rm[9], tv[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Rm[q] = sp->Rf[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) tv[q] = sp->tf[q];
+    const float kap_uniform = sp->kap;
     Src src[S];
     Acc acc[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int nl = warp * 32 * S + s * 32 + lane;
+    for (int s2 = 0; s2 < S; ++s2) {
+      const int nl = warp * 32 * S + s2 * 32 + lane;
       const long long n = static_cast<long long>(b) * SB + nl;
       const float4 x = xs[n];
-      // z = R x + t in FP32 (centred frame)
+      // z = R x + t in FP32 (centred frame of the pair)
       const float z0 = fmaf(Rm[0], x.x, fmaf(Rm[1], x.y, fmaf(Rm[2], x.z, tv[0])));
       const float z1 = fmaf(Rm[3], x.x, fmaf(Rm[4], x.y, fmaf(Rm[5], x.z, tv[1])));
       const float z2 = fmaf(Rm[6], x.x, fmaf(Rm[7], x.y, fmaf(Rm[8], x.z, tv[2])));
-      src[s].z0 = dup(z0);
-      src[s].z1 = dup(z1);
-      src[s].z2 = dup(z2);
-      src[s].kp = dup(kap_n ? kap_n[n] : kap_uniform);
+      src[s2].z0 = dup(z0);
+      src[s2].z1 = dup(z1);
+      src[s2].z2 = dup(z2);
+      src[s2].kp = dup(kap_n ? kap_n[n] : kap_uniform);
       const float2 zero = make_float2(0.f, 0.f);
-      acc[s] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
+      acc[s2] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
     }
 
     for (; u < seg_end; ++u, ++i) {
@@ -266,15 +284,14 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
         abort = true;
         break;
       }
-      if (tid == 0 && i + kStages < n_units) {
-        const long long tile = (u0 + i + kStages) % num_tiles;
-        bulk_load(tiles + stage * kTileFloats, rec + tile * kTileFloats, kTileBytes, &full[stage]);
-      }
+      if (tid == 0 && i + kStages < n_units)
+        bulk_load(tiles + stage * kTileFloats, rec + tile_of(u0 + i + kStages) * kTileFloats, kTileBytes,
+                  &full[stage]);
     }
     if (abort) break;
-    float* dst = part + static_cast<size_t>(table[blockIdx.x] + seg) * kMom * SB;
+    float* dst = part + static_cast<size_t>(first_slot + seg) * kMom * SB;
 #pragma unroll
-    for (int s = 0; s < S; ++s) store_acc(dst, SB, warp * 32 * S + s * 32 + lane, acc[s]);
+    for (int s2 = 0; s2 < S; ++s2) store_acc(dst, SB, warp * 32 * S + s2 * 32 + lane, acc[s2]);
     ++seg;
   }
   if (abort && tid == 0) {
@@ -288,32 +305,38 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
 
 // ---------------------------------------------------------------------------
 // Per-source shift for the max-shift mode (used when w = 0 or the fixed shift
-// could overflow FP32): L_n = max(log2 gamma, max_m (l_m - c d_mn)).
+// could overflow FP32): L_n = max(log2 gamma, max_m (l_m - c d_mn)) over the
+// targets of the source's pair.
 // ---------------------------------------------------------------------------
 constexpr int kShiftThreads = 128;
 
-__global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __restrict__ xs,
-                                                              const float* __restrict__ rec,
-                                                              const EmState* __restrict__ st,
-                                                              long long N, int num_tiles,
-                                                              float* __restrict__ kap_n,
-                                                              float* __restrict__ gam_n) {
+__global__ void __launch_bounds__(kShiftThreads)
+    shift_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
+                 const int* __restrict__ tab, const long long* __restrict__ off64,
+                 const int* __restrict__ done_count, float* __restrict__ kap_n, float* __restrict__ gam_n, Geo g) {
   __shared__ __align__(16) float tile[7 * kTile];
-  if (st->done) return;
+  if (*done_count >= g.P) return;
+  // every CTA covers kShiftThreads sources of one source block (SB is a multiple)
   const long long n = static_cast<long long>(blockIdx.x) * kShiftThreads + threadIdx.x;
-  const bool valid = n < N;
-  const float4 x = valid ? xs[n] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float* R = st->Rf;
-  const float z0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, st->tf[0])));
-  const float z1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, st->tf[1])));
-  const float z2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, st->tf[2])));
-  const float nc = st->neg_c;
+  const int b = static_cast<int>(n / g.SB);
+  const int pair = tab[g.o_block_pair + b];
+  const long long local = n - static_cast<long long>(tab[g.o_blk_off + pair]) * g.SB;
+  const long long Np = off64[pair + 1] - off64[pair];
+  const bool valid = local < Np;
+  const EmState* sp = st + pair;
+  const float4 x = xs[n];
+  const float* R = sp->Rf;
+  const float z0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, sp->tf[0])));
+  const float z1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, sp->tf[1])));
+  const float z2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, sp->tf[2])));
+  const float nc = sp->neg_c;
   float best = -INFINITY;
-  for (int t = 0; t < num_tiles; ++t) {
+  const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
+  for (int t = t0; t < t1; ++t) {
     __syncthreads();
     for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) {
-      const int p = e / kTile, j = e % kTile;
-      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + (p < 6 ? p : 12) * kTile + j];
+      const int pl = e / kTile, j = e % kTile;
+      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + (pl < 6 ? pl : 12) * kTile + j];
     }
     __syncthreads();
 #pragma unroll 4
@@ -321,14 +344,13 @@ __global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __re
       const float r0 = z0 + tile[0 * kTile + j];
       const float r1 = z1 + tile[1 * kTile + j];
       const float r2 = z2 + tile[2 * kTile + j];
-      const float v = fmaf(tile[3 * kTile + j], r0,
-                           fmaf(tile[4 * kTile + j], r1, tile[5 * kTile + j] * r2));
+      const float v = fmaf(tile[3 * kTile + j], r0, fmaf(tile[4 * kTile + j], r1, tile[5 * kTile + j] * r2));
       const float d = fmaf(v, v, fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
       best = fmaxf(best, fmaf(d, nc, tile[6 * kTile + j]));
     }
   }
   if (!valid) return;
-  const float Lg = st->L;  // log2 gamma (-inf without outlier term)
+  const float Lg = sp->L;  // log2 gamma (-inf without outlier term)
   const float L = fmaxf(best, Lg);
   // kappa = L / c with c = -neg_c; gamma' = 2^(log2 gamma - L)
   kap_n[n] = -L / nc;
@@ -341,123 +363,120 @@ __global__ void __launch_bounds__(kShiftThreads) shift_kernel(const float4* __re
 // moments of the M step (FP32 products).  Each warp transposes its 32 x 76
 // contributions through shared memory; lane l then sums columns l, l+32, l+64
 // over the 32 sources with Neumaier's compensated summation (an error-free
-// TwoSum per add), and adds the result to FP64 per-warp accumulators.  FP64
-// appears only there and in the cross-block reduction.
+// TwoSum per add), and the CTA adds its warps in FP64.  A CTA covers
+// kCombineSources sources of one source block (hence of one pair) and writes
+// one row of kGlob doubles; FP64 appears only there and in the per-pair
+// cross-row reduction.
 // ---------------------------------------------------------------------------
-constexpr int kCombineThreads = 128;
+constexpr int kCombineThreads = kCombineSources;
 constexpr int kCombineWarps = kCombineThreads / 32;
 constexpr int kCPad = kGlob + 1;  // odd row pitch: conflict-free transposition
 
 __global__ void __launch_bounds__(kCombineThreads)
-    combine_kernel(const float4* __restrict__ xs, long long N, const float* __restrict__ part,
-                   const int* __restrict__ table, const EmState* __restrict__ st,
-                   const float* __restrict__ kap_n, const float* __restrict__ gam_n,
-                   double* __restrict__ rows, float* __restrict__ per_n, int SB, int grid_e) {
+    combine_kernel(const float4* __restrict__ xs, const float* __restrict__ part, const int* __restrict__ tab,
+                   const long long* __restrict__ off64, const EmState* __restrict__ st,
+                   const int* __restrict__ done_count, const float* __restrict__ kap_n,
+                   const float* __restrict__ gam_n, double* __restrict__ rows, float* __restrict__ per_n, Geo g) {
   __shared__ float buf[kCombineWarps][32 * kCPad];
   __shared__ double acc[kCombineWarps][kGlob];
-  if (st->done) return;
+  if (*done_count >= g.P) return;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  for (int j = lane; j < kGlob; j += 32) acc[warp][j] = 0.0;
-  const float kap_u = st->kap;
-  const float L_u = st->L;
-  const float gp_u = (st->log2_wodds > -INFINITY) ? 1.f : 0.f;
-  const float nc = st->neg_c;
-  const float nll_c = static_cast<float>(st->nll_const);
-  const long long stride = static_cast<long long>(gridDim.x) * kCombineThreads;
+  const long long n = static_cast<long long>(blockIdx.x) * kCombineThreads + tid;
+  const int b = static_cast<int>(n / g.SB);
+  const int pair = tab[g.o_block_pair + b];
+  const EmState* sp = st + pair;
+  if (sp->done) return;  // uniform over the CTA: its rows are not read again
+  const long long local = n - static_cast<long long>(tab[g.o_blk_off + pair]) * g.SB;
+  const long long Np = off64[pair + 1] - off64[pair];
+  const bool valid = local < Np;
+  const int nl = static_cast<int>(n - static_cast<long long>(b) * g.SB);
+  float m[kMom], cmp[kMom];
+#pragma unroll
+  for (int k = 0; k < kMom; ++k) m[k] = cmp[k] = 0.f;
+  float x0 = 0.f, x1 = 0.f, x2 = 0.f, kap = 0.f, gp = 0.f, L = 0.f;
+  if (valid) {
+    const int first = tab[g.o_block_slot + 2 * b];
+    const int count = tab[g.o_block_slot + 2 * b + 1];
+    for (int j = first; j < first + count; ++j) {
+      const float* src = part + static_cast<size_t>(j) * kMom * g.SB + nl;
+#pragma unroll
+      for (int k = 0; k < kMom; ++k) {  // Kahan summation of the pieces
+        const float y = src[static_cast<size_t>(k) * g.SB] - cmp[k];
+        const float t = m[k] + y;
+        cmp[k] = (t - m[k]) - y;
+        m[k] = t;
+      }
+    }
+    const float4 x = xs[n];
+    x0 = x.x;
+    x1 = x.y;
+    x2 = x.z;
+    if (kap_n) {
+      kap = kap_n[n];
+      gp = gam_n[n];
+      L = -kap * sp->neg_c;
+    } else {
+      kap = sp->kap;
+      gp = (sp->log2_wodds > -INFINITY) ? 1.f : 0.f;
+      L = sp->L;
+    }
+  }
+  const float S0 = m[0];
+  const float D = m[10] - kap * S0;
+  const float denom = S0 + gp;
+  const float inv = denom > 0.f ? 1.f / denom : 0.f;
+  const float Pb = S0 * inv;
+  const float h[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
+  const float W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv, W12 = m[8] * inv,
+              W22 = m[9] * inv;
+  const float Dn = D * inv;
+  const float Pout = gp * inv;
+  const float nll_c = static_cast<float>(sp->nll_const);
+  const float nll = (valid && denom > 0.f) ? nll_c - (L * 0.6931471805599453f + logf(denom)) : 0.f;
+  if (valid && per_n) {
+    float4* o = reinterpret_cast<float4*>(per_n + (off64[pair] + local) * 16);
+    o[0] = make_float4(Pb, h[0], h[1], h[2]);
+    o[1] = make_float4(W00, W01, W02, W11);
+    o[2] = make_float4(W12, W22, Dn, Pout);
+    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
+  const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
   float* row = buf[warp] + lane * kCPad;
-  // every warp runs the same number of chunk iterations
-  for (long long base = static_cast<long long>(blockIdx.x) * kCombineThreads; base < N; base += stride) {
-    const long long n = base + tid;
-    const bool valid = n < N;
-    float m[kMom], cmp[kMom];
+  row[0] = Pb;
+  row[1] = Dn;
 #pragma unroll
-    for (int k = 0; k < kMom; ++k) m[k] = cmp[k] = 0.f;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f, kap = 0.f, gp = 0.f, L = 0.f;
-    if (valid) {
-      const int b = static_cast<int>(n / SB);
-      const int nl = static_cast<int>(n - static_cast<long long>(b) * SB);
-      const int first = table[grid_e + 1 + 2 * b];
-      const int count = table[grid_e + 2 + 2 * b];
-      for (int j = first; j < first + count; ++j) {
-        const float* src = part + static_cast<size_t>(j) * kMom * SB + nl;
+  for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int k = 0; k < kMom; ++k) {  // Kahan summation of the pieces
-          const float y = src[static_cast<size_t>(k) * SB] - cmp[k];
-          const float t = m[k] + y;
-          cmp[k] = (t - m[k]) - y;
-          m[k] = t;
-        }
-      }
-      const float4 x = xs[n];
-      x0 = x.x;
-      x1 = x.y;
-      x2 = x.z;
-      if (kap_n) {
-        kap = kap_n[n];
-        gp = gam_n[n];
-        L = -kap * nc;
-      } else {
-        kap = kap_u;
-        gp = gp_u;
-        L = L_u;
-      }
-    }
-    const float S0 = m[0];
-    const float D = m[10] - kap * S0;
-    const float denom = S0 + gp;
-    const float inv = denom > 0.f ? 1.f / denom : 0.f;
-    const float Pb = S0 * inv;
-    const float h[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
-    const float W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv,
-                W12 = m[8] * inv, W22 = m[9] * inv;
-    const float Dn = D * inv;
-    const float Pout = gp * inv;
-    const float nll = (valid && denom > 0.f) ? nll_c - (L * 0.6931471805599453f + logf(denom)) : 0.f;
-    if (valid && per_n) {
-      float4* o = reinterpret_cast<float4*>(per_n + n * 16);
-      o[0] = make_float4(Pb, h[0], h[1], h[2]);
-      o[1] = make_float4(W00, W01, W02, W11);
-      o[2] = make_float4(W12, W22, Dn, Pout);
-      o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
-    const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
-    row[0] = Pb;
-    row[1] = Dn;
+    for (int k = 0; k < 4; ++k) row[2 + 4 * i + k] = h[i] * xt[k];
+  {
+    int j = 14;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int p = 0; p < 6; ++p)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) row[2 + 4 * i + k] = h[i] * xt[k];
-    {
-      int j = 14;
+      for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int p = 0; p < 6; ++p)
+        for (int l = k; l < 4; ++l) row[j++] = A[p] * (xt[k] * xt[l]);
+  }
+  row[74] = Pout;
+  row[75] = nll;
+  __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-          for (int l = k; l < 4; ++l) row[j++] = A[p] * (xt[k] * xt[l]);
-    }
-    row[74] = Pout;
-    row[75] = nll;
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int col = lane + 32 * i;
-      if (col < kGlob) {
-        float sum = 0.f, comp = 0.f;
+  for (int i = 0; i < 3; ++i) {
+    const int col = lane + 32 * i;
+    if (col < kGlob) {
+      float sum = 0.f, comp = 0.f;
 #pragma unroll 8
-        for (int r = 0; r < 32; ++r) {  // Neumaier: sum + comp is the exact running sum
-          const float v = buf[warp][r * kCPad + col];
-          const float t = sum + v;
-          comp += (fabsf(sum) >= fabsf(v)) ? ((sum - t) + v) : ((v - t) + sum);
-          sum = t;
-        }
-        acc[warp][col] += static_cast<double>(sum) + static_cast<double>(comp);
+      for (int r = 0; r < 32; ++r) {  // Neumaier: sum + comp is the exact running sum
+        const float v = buf[warp][r * kCPad + col];
+        const float t = sum + v;
+        comp += (fabsf(sum) >= fabsf(v)) ? ((sum - t) + v) : ((v - t) + sum);
+        sum = t;
       }
+      acc[warp][col] = static_cast<double>(sum) + static_cast<double>(comp);
     }
-    __syncwarp();
   }
   __syncthreads();
   if (tid < kGlob) {
@@ -468,25 +487,34 @@ __global__ void __launch_bounds__(kCombineThreads)
   }
 }
 
-// One warp per global moment: lanes take strided rows, then a shuffle tree (FP64).
-__global__ void final_reduce_kernel(const double* __restrict__ rows, int nrows, double* __restrict__ mom,
-                                    const EmState* __restrict__ st) {
-  if (st && st->done) return;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+// One warp per (pair, moment): lanes take strided rows of the pair, then a
+// shuffle tree (FP64).
+constexpr int kReduceWarps = 4;
+
+__global__ void final_reduce_kernel(const double* __restrict__ rows, const int* __restrict__ tab,
+                                    const EmState* __restrict__ st, const int* __restrict__ done_count,
+                                    double* __restrict__ mom, Geo g) {
+  if (*done_count >= g.P) return;
+  const int pair = blockIdx.y;
+  if (st[pair].done) return;
+  const int j = blockIdx.x * kReduceWarps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (j >= kGlob) return;
+  const int per_block = g.SB / kCombineSources;
+  const int r0 = tab[g.o_blk_off + pair] * per_block;
+  const int r1 = tab[g.o_blk_off + pair + 1] * per_block;
   double v = 0.0;
-  for (int r = lane; r < nrows; r += 32) v += rows[static_cast<size_t>(r) * kGlob + j];
+  for (int r = r0 + lane; r < r1; r += 32) v += rows[static_cast<size_t>(r) * kGlob + j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane == 0) mom[j] = v;
+  if (lane == 0) mom[static_cast<size_t>(pair) * kGlob + j] = v;
 }
 
 template <int S>
-cudaError_t launch_estep_t(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                           const float* kap_n, float* part, const int* table, int* status, cudaStream_t s) {
-  estep_kernel<S><<<p.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, st, kap_n, part, table, status,
-                                                                   p.num_tiles, p.units, p.seg_cap);
+cudaError_t launch_estep_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
+                           const float* kap_n, float* part, int* status, cudaStream_t s) {
+  estep_kernel<S><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, kap_n, part, d.tab,
+                                                                     d.done_count, status, p.g);
   return cudaGetLastError();
 }
 
@@ -507,107 +535,160 @@ int resident_ctas(int S) {
   return occ;
 }
 
-}  // namespace
-
 int warps_of(int S) { return S >= 4 ? warps_for<4>() : (S == 2 ? warps_for<2>() : warps_for<1>()); }
 
-EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override) {
-  EstepPlan p{};
-  p.num_tiles = static_cast<int>((M + kTile - 1) / kTile);
+}  // namespace
+
+BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
+                     int S_override) {
+  BatchPlan p{};
+  Geo& g = p.g;
+  const int P = static_cast<int>(N.size());
+  g.P = P;
   p.smem_bytes = kStages * kTileBytes + kStages * sizeof(uint64_t);
+  std::vector<int> tiles(P);
+  long long T = 0;
+  g.max_n = 0;
+  g.max_m = 0;
+  g.max_tiles = 0;
+  for (int i = 0; i < P; ++i) {
+    tiles[i] = static_cast<int>((M[i] + kTile - 1) / kTile);
+    T += tiles[i];
+    if (N[i] > g.max_n) g.max_n = N[i];
+    if (M[i] > g.max_m) g.max_m = M[i];
+    if (tiles[i] > g.max_tiles) g.max_tiles = tiles[i];
+  }
+  g.T = static_cast<int>(T);
+  auto units_for = [&](int S) {
+    const int SB = warps_of(S) * 32 * S;
+    long long U = 0;
+    for (int i = 0; i < P; ++i) U += ((N[i] + SB - 1) / SB) * static_cast<long long>(tiles[i]);
+    return U;
+  };
   int chosen = 1;
   if (S_override == 1 || S_override == 2 || S_override == 4) {
     chosen = S_override;
   } else {
     const int cands[3] = {4, 2, 1};
     for (int c : cands) {
+      // enough units for a balanced grid, and not much padding per pair
       const int SB = warps_of(c) * 32 * c;
-      const long long blocks = (N + SB - 1) / SB;
-      const long long units = blocks * p.num_tiles;
-      if (units >= 4LL * num_sms * resident_ctas(c)) {
+      long long pad = 0, tot = 0;
+      for (int i = 0; i < P; ++i) {
+        pad += ((N[i] + SB - 1) / SB) * SB - N[i];
+        tot += N[i];
+      }
+      if (units_for(c) >= 4LL * num_sms * resident_ctas(c) && pad * 20 <= tot) {
         chosen = c;
         break;
       }
     }
   }
-  p.S = chosen;
-  p.NW = warps_of(chosen);
-  p.SB = p.NW * 32 * chosen;
-  p.num_blocks = static_cast<int>((N + p.SB - 1) / p.SB);
-  p.units = static_cast<long long>(p.num_blocks) * p.num_tiles;
+  g.S = chosen;
+  g.SB = warps_of(chosen) * 32 * chosen;
+  g.seg_cap = 64;
+  // pair tables
+  std::vector<int> blk_off(P + 1, 0), tile_off(P + 1, 0);
+  g.max_blocks = 0;
+  for (int i = 0; i < P; ++i) {
+    const int nb = static_cast<int>((N[i] + g.SB - 1) / g.SB);
+    blk_off[i + 1] = blk_off[i] + nb;
+    tile_off[i + 1] = tile_off[i] + tiles[i];
+    if (nb > g.max_blocks) g.max_blocks = nb;
+  }
+  g.B = blk_off[P];
+  std::vector<int> block_pair(g.B), unit_off(g.B + 1, 0);
+  for (int i = 0; i < P; ++i)
+    for (int b = blk_off[i]; b < blk_off[i + 1]; ++b) {
+      block_pair[b] = i;
+      unit_off[b + 1] = unit_off[b] + tiles[i];
+    }
+  g.U = unit_off[g.B];
   const long long slots = static_cast<long long>(num_sms) * resident_ctas(chosen);
-  p.grid = static_cast<int>(p.units < slots ? p.units : slots);
-  p.seg_cap = 64;
+  g.grid = static_cast<int>(g.U < slots ? g.U : slots);
   // slot table: replay the kernel's segmentation (same rules, host side)
-  p.table.assign(static_cast<size_t>(p.grid) + 1 + 2 * static_cast<size_t>(p.num_blocks), 0);
-  std::vector<int> first(p.num_blocks, -1), count(p.num_blocks, 0);
+  std::vector<int> cta_slot(g.grid + 1, 0), cta_block(g.grid, 0), first(g.B, -1), count(g.B, 0);
   int slot = 0;
-  for (int c = 0; c < p.grid; ++c) {
-    p.table[c] = slot;
-    const long long u0 = static_cast<long long>(c) * p.units / p.grid;
-    const long long u1 = static_cast<long long>(c + 1) * p.units / p.grid;
+  int b = 0;
+  for (int c = 0; c < g.grid; ++c) {
+    cta_slot[c] = slot;
+    const long long u0 = static_cast<long long>(c) * g.U / g.grid;
+    const long long u1 = static_cast<long long>(c + 1) * g.U / g.grid;
+    while (u0 >= unit_off[b + 1]) ++b;
+    cta_block[c] = b;
     long long u = u0;
+    int bb = b;
     while (u < u1) {
-      const int b = static_cast<int>(u / p.num_tiles);
-      long long e = u + p.seg_cap;
-      const long long be = static_cast<long long>(b + 1) * p.num_tiles;
-      if (e > be) e = be;
+      while (u >= unit_off[bb + 1]) ++bb;
+      long long e = u + g.seg_cap;
+      if (e > unit_off[bb + 1]) e = unit_off[bb + 1];
       if (e > u1) e = u1;
-      if (first[b] < 0) first[b] = slot;
-      ++count[b];
+      if (first[bb] < 0) first[bb] = slot;
+      ++count[bb];
       ++slot;
       u = e;
     }
   }
-  p.table[p.grid] = slot;
-  p.total_slots = slot;
-  for (int b = 0; b < p.num_blocks; ++b) {
-    p.table[p.grid + 1 + 2 * b] = first[b];
-    p.table[p.grid + 2 + 2 * b] = count[b];
+  cta_slot[g.grid] = slot;
+  g.total_slots = slot;
+  g.combine_ctas = g.B * (g.SB / kCombineSources);
+  // pack the device table
+  auto& t = p.tab;
+  t.clear();
+  auto put = [&](const std::vector<int>& v) {
+    const int o = static_cast<int>(t.size());
+    t.insert(t.end(), v.begin(), v.end());
+    return o;
+  };
+  g.o_blk_off = put(blk_off);
+  g.o_tile_off = put(tile_off);
+  g.o_block_pair = put(block_pair);
+  g.o_unit_off = put(unit_off);
+  g.o_cta_slot = put(cta_slot);
+  g.o_cta_block = put(cta_block);
+  std::vector<int> bs(2 * static_cast<size_t>(g.B));
+  for (int q = 0; q < g.B; ++q) {
+    bs[2 * q] = first[q];
+    bs[2 * q + 1] = count[q];
+  }
+  g.o_block_slot = put(bs);
+  p.off64.assign(2 * static_cast<size_t>(P) + 2, 0);
+  for (int i = 0; i < P; ++i) {
+    p.off64[i + 1] = p.off64[i] + N[i];
+    p.off64[P + 1 + i + 1] = p.off64[P + 1 + i] + M[i];
   }
   return p;
 }
 
-size_t estep_partial_floats(const EstepPlan& p) {
-  return static_cast<size_t>(p.total_slots) * kMom * p.SB;
-}
+size_t estep_partial_floats(const Geo& g) { return static_cast<size_t>(g.total_slots) * kMom * g.SB; }
 
-cudaError_t launch_estep(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         const float* kap_n, float* part, const int* table, int* status, cudaStream_t s) {
-  switch (p.S) {
-    case 4: return launch_estep_t<4>(p, xs, rec, st, kap_n, part, table, status, s);
-    case 2: return launch_estep_t<2>(p, xs, rec, st, kap_n, part, table, status, s);
-    default: return launch_estep_t<1>(p, xs, rec, st, kap_n, part, table, status, s);
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
+                         const float* kap_n, float* part, int* status, cudaStream_t s) {
+  switch (p.g.S) {
+    case 4: return launch_estep_t<4>(p, d, xs, rec, kap_n, part, status, s);
+    case 2: return launch_estep_t<2>(p, d, xs, rec, kap_n, part, status, s);
+    default: return launch_estep_t<1>(p, d, xs, rec, kap_n, part, status, s);
   }
 }
 
-cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         int64_t N, float* kap_n, float* gam_n, cudaStream_t s) {
-  const long long blocks = (N + kShiftThreads - 1) / kShiftThreads;
-  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, st, N, p.num_tiles,
-                                                                      kap_n, gam_n);
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* kap_n,
+                         float* gam_n, cudaStream_t s) {
+  const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
+  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.off64,
+                                                                      d.done_count, kap_n, gam_n, p.g);
   return cudaGetLastError();
 }
 
-int combine_rows(int64_t N, int num_sms) {
-  const long long b = (N + kCombineThreads - 1) / kCombineThreads;
-  const long long cap = 4LL * num_sms;
-  return static_cast<int>(b < cap ? b : cap);
-}
-
-cudaError_t launch_combine(const EstepPlan& p, const float4* xs, int64_t N, const float* part,
-                           const int* table, const EmState* st, const float* kap_n, const float* gam_n,
-                           double* rows, int nrows, float* per_n, cudaStream_t s) {
-  combine_kernel<<<nrows, kCombineThreads, 0, s>>>(xs, N, part, table, st, kap_n, gam_n, rows, per_n, p.SB,
-                                                   p.grid);
+cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part,
+                           const float* kap_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s) {
+  combine_kernel<<<p.g.combine_ctas, kCombineThreads, 0, s>>>(xs, part, d.tab, d.off64, d.st, d.done_count,
+                                                              kap_n, gam_n, rows, per_n, p.g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_final_reduce(const double* rows, int nrows, double* mom, const EmState* st,
-                                cudaStream_t s) {
-  const int warps_per_block = 4;
-  const int blocks = (kGlob + warps_per_block - 1) / warps_per_block;
-  final_reduce_kernel<<<blocks, 32 * warps_per_block, 0, s>>>(rows, nrows, mom, st);
+cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom, cudaStream_t s) {
+  dim3 grid((kGlob + kReduceWarps - 1) / kReduceWarps, static_cast<unsigned>(p.g.P));
+  final_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(rows, d.tab, d.st, d.done_count, mom, p.g);
   return cudaGetLastError();
 }
 

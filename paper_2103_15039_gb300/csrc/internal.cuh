@@ -1,4 +1,9 @@
 // Internal declarations shared by the CUDA translation units of liblsgcpd.
+//
+// Every kernel works on a batch of P independent registration pairs (a single
+// registration is a batch of one).  Pair i has N_i sources and M_i targets;
+// the raw inputs are concatenated (offsets n_off / m_off), sources are padded
+// per pair to whole source blocks of SB and targets to whole tiles of kTile.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,9 +14,9 @@
 namespace lsg {
 
 // ---------------------------------------------------------------------------
-// Target records (one per target y_m, in the centred frame), stored tile-major
-// and plane-minor so that a tile of kTile targets is one contiguous block that
-// a single bulk copy moves into shared memory:
+// Target records (one per target y_m, in its pair's centred frame), stored
+// tile-major and plane-minor so that a tile of kTile targets is one contiguous
+// block that a single bulk copy moves into shared memory:
 //   rec[tile][plane][kTile]
 // planes: -y (3), a = sqrt(alpha) n (3), a a^T (00,01,02,11,12,22), l
 // with l = log2 pi_m (+ 1/2 log2(1 + alpha_m) with the Gaussian constant).
@@ -27,15 +32,19 @@ constexpr int kTileBytes = kTileFloats * 4;
 //   D' = sum e (d + kappa_n)
 constexpr int kMom = 11;
 
-// Global moments (see lsgcpd.h): N_P, sum D, H1 (12), G (60), sum Pout, NLL part.
+// Global moments per pair (see lsgcpd.h): N_P, sum D, H1 (12), G (60), sum Pout, NLL.
 constexpr int kGlob = 76;
+
+// Sources per combine CTA (a divisor of every source block size).
+constexpr int kCombineSources = 128;
 
 // Status bits written by kernels (never traps).
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusNumeric = 2;
 
-// Device-resident EM state.  Written by the initialisation and M-step kernels,
-// read by the E step, so that a whole EM loop runs without the host.
+// Device-resident EM state of one pair.  Written by the initialisation and
+// M-step kernels, read by the E step, so that a whole EM loop runs without the
+// host.
 struct EmState {
   double R[9];          // current g in the centred frame
   double t[3];
@@ -76,7 +85,7 @@ __device__ inline void set_estep_constants(EmState* st) {
   st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
 }
 
-// Scalar parameters the device needs (a subset of lsgcpd_params, plus sizes).
+// Scalar parameters the device needs (a subset of lsgcpd_params).
 struct DevParams {
   double w;
   double volume;
@@ -92,70 +101,102 @@ struct DevParams {
   int32_t pad;
 };
 
-// Launch plan of the hot E-step kernel: a stream-K style split of
-// (source block) x (target tile) units over a grid sized to the SM count.
-// A CTA flushes its partial moments into a new slot at every source-block
-// boundary and every seg_cap tiles.  Slots are numbered CTA-major, so all
-// slots of one source block are contiguous.  `table` holds, for the device:
-//   [0, grid]                first slot of every CTA (prefix sums)
-//   [grid+1, grid+1+2*blocks) (first slot, slot count) of every source block
-struct EstepPlan {
-  int S;               // sources per thread
-  int NW;              // warps per CTA
-  int SB;              // sources per block = NW * 32 * S
-  int num_blocks;      // ceil(N / SB)
-  int num_tiles;       // ceil(M / kTile)
-  long long units;     // num_blocks * num_tiles
-  int grid;            // CTAs (<= units)
-  int seg_cap;         // flush after this many tiles (FP32 sums stay short)
+// ---------------------------------------------------------------------------
+// Batch geometry: sizes, layouts and the E step's stream-K work split.
+//
+// Work = (source block) x (target tile of the block's pair) units, ordered
+// block-major, split into `grid` contiguous ranges (one per CTA).  A CTA
+// flushes its partial moments into a new slot at every source-block boundary
+// and every seg_cap tiles; slots are numbered CTA-major, so all slots of one
+// source block are contiguous.
+//
+// Device int32 table (offsets in Geo):
+//   blk_off[P+1]    first source block of each pair
+//   tile_off[P+1]   first target tile of each pair
+//   block_pair[B]   pair of each source block
+//   unit_off[B+1]   first unit of each source block
+//   cta_slot[G+1]   first partial slot of each CTA
+//   cta_block[G]    source block of each CTA's first unit
+//   block_slot[2B]  (first slot, slot count) of each source block
+// Device int64 table: n_off[P+1], m_off[P+1] (offsets of the raw inputs).
+// ---------------------------------------------------------------------------
+struct Geo {
+  int P;
+  int S;               // sources per thread of the E step
+  int SB;              // sources per source block
+  int B;               // source blocks
+  int T;               // target tiles
+  int grid;            // E-step CTAs
+  int seg_cap;
+  int max_tiles;       // largest tile count of one pair
+  int max_blocks;      // largest source-block count of one pair
+  long long U;         // units
+  long long max_n;     // largest N_i
+  long long max_m;     // largest M_i
+  int o_blk_off, o_tile_off, o_block_pair, o_unit_off, o_cta_slot, o_cta_block, o_block_slot;
   int total_slots;
-  size_t smem_bytes;
-  std::vector<int> table;
+  int combine_ctas;    // B * SB / kCombineSources
 };
 
-// ----- kernels / launchers (estep.cu) -------------------------------------
-EstepPlan plan_estep(int64_t N, int64_t M, int num_sms, int S_override);
-size_t estep_partial_floats(const EstepPlan& p);
-cudaError_t launch_estep(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         const float* kap_n, float* part, const int* table, int* status,
-                         cudaStream_t s);
-cudaError_t launch_shift(const EstepPlan& p, const float4* xs, const float* rec, const EmState* st,
-                         int64_t N, float* kap_n, float* gam_n, cudaStream_t s);
-// rows of FP64 partial global moments written by the combine kernel
-int combine_rows(int64_t N, int num_sms);
-cudaError_t launch_combine(const EstepPlan& p, const float4* xs, int64_t N, const float* part,
-                           const int* table, const EmState* st, const float* kap_n,
-                           const float* gam_n, double* rows, int nrows, float* per_n,
+struct BatchPlan {
+  Geo g;
+  std::vector<int> tab;
+  std::vector<long long> off64;  // n_off[P+1], m_off[P+1]
+  size_t smem_bytes;
+};
+
+// Plan a batch (sizes N[i], M[i]); S_override in {1, 2, 4} forces the
+// sources per thread, 0 chooses.
+BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
+                     int S_override);
+size_t estep_partial_floats(const Geo& g);
+
+// Device pointers of a batch.
+struct Dev {
+  const int* tab;
+  const long long* off64;
+  EmState* st;         // [P]
+  int* done_count;     // number of pairs whose EM loop has finished
+};
+
+// ----- E step (estep.cu) --------------------------------------------------------
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
+                         const float* kap_n, float* part, int* status, cudaStream_t s);
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* kap_n,
+                         float* gam_n, cudaStream_t s);
+cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part,
+                           const float* kap_n, const float* gam_n, double* rows, float* per_n,
                            cudaStream_t s);
-// Sum the rows (fixed order, FP64) into kGlob moments; one warp per moment.
-cudaError_t launch_final_reduce(const double* rows, int nrows, double* mom, const EmState* st,
+// Sum each pair's combine rows (fixed order, FP64) into mom[P][kGlob]; one warp per moment.
+cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom,
                                 cudaStream_t s);
 
 // ----- M step (mstep.cu) -------------------------------------------------------
-// Newton M step from the kGlob global moments `mom` and the state update.
-cudaError_t launch_mstep(const double* mom, EmState* st, const DevParams& dp, double* trace,
-                         cudaStream_t s);
+// Newton M step of every pair from mom[P][kGlob] and the state update; trace [P][iters][8].
+cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* mom, const DevParams& dp,
+                         double* trace, int trace_iters, cudaStream_t s);
 // Standalone M step: io[0..75] moments, io[80..91] starting pose (R, t);
 // results R (9), t (3), sigma2, Q, newton steps, damped, halvings at io[96..112].
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s);
+// E-step constants of pair 0 for a pose given in the caller's frame (centroids known).
+cudaError_t launch_estep_constants(EmState* st, double sigma2, double w, double V, const double* R,
+                                   const double* t, cudaStream_t s);
 
 // ----- preprocessing / initialisation (prep.cu) ------------------------------
-int stats_blocks(int64_t n);
-cudaError_t launch_init(const float* X, int64_t N, const float* Y, int64_t M, const DevParams& dp,
-                        double* red, EmState* st, float4* xs, int64_t n_pad, cudaStream_t s);
-cudaError_t launch_center_only(const float* X, int64_t N, const float* Y, int64_t M, double* red,
-                               EmState* st, float4* xs, int64_t n_pad, cudaStream_t s);
-cudaError_t launch_knn(const float* Y, int64_t M, int k, float4* y4, float* part_d, int* part_i,
-                       int* idx_out, int splits, cudaStream_t s);
-int knn_splits(int64_t M, int num_sms);
-cudaError_t launch_geometry(const float* Y, int64_t M, const int* idx, int k, double alpha_max,
-                            double lambda, int alpha_norm, const EmState* st, float* rec,
-                            int num_tiles, float* normals, float* kappa, float* alpha,
-                            cudaStream_t s);
-cudaError_t launch_pack(const float* Y, const float* normals, const float* alpha, int64_t M,
-                        int alpha_norm, const EmState* st, float* rec, int num_tiles,
-                        cudaStream_t s);
-cudaError_t launch_estep_constants(EmState* st, double sigma2, double w, double V,
-                                   const double* R, const double* t, cudaStream_t s);
+// Rows of the statistics reductions per pair.
+int stats_chunks(const Geo& g);
+// Centroids, AABB, V, floor and centred sources of every pair; with `full`, also
+// sigma^2_0 and the initial EM state (otherwise only what the standalone E step
+// and the preprocessing need).
+cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const DevParams& dp,
+                        bool full, double* red, float4* xs, cudaStream_t s);
+int knn_splits(const Geo& g, int num_sms);
+cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, int splits, float4* y4,
+                       float* part_d, int* part_i, int* idx_out, cudaStream_t s);
+cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
+                            double alpha_max, double lambda, int alpha_norm, float* rec, float* normals,
+                            float* kappa, float* alpha, cudaStream_t s);
+cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals,
+                        const float* alpha, int alpha_norm, float* rec, cudaStream_t s);
 
 }  // namespace lsg

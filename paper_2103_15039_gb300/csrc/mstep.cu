@@ -163,12 +163,6 @@ struct Shared {
 // position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
 __host__ __device__ constexpr int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
 
-// row / column of the i-th entry of the upper triangle of a 6x6 matrix
-__constant__ int c_hrow[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
-__constant__ int c_hcol[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
-
-
-
 __device__ __forceinline__ int pair_q(int k, int l) {
   if (k > l) {
     const int t = k;
@@ -186,11 +180,6 @@ __device__ __forceinline__ int sym_p(int i, int j) {
     j = t;
   }
   return i == 0 ? j : (i == 1 ? 2 + j : 5);
-}
-
-__device__ __forceinline__ double Aent(const Shared& s, int q, int i, int j) { return s.A[q][sym_p(i, j)]; }
-__device__ __forceinline__ double Cent(const Shared& s, int k, int l, int i, int j) {
-  return s.C[pair_q(k, l)][3 * i + j];
 }
 
 // Levi-Civita symbol for indices in {0, 1, 2}
@@ -421,7 +410,6 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       if (tid < 32) {  // G D and dQ = 2 <M1, D> + <D, G D>
         double dq = 0.0;
         if (tid < 12) {
-          const int i = tid / 4, k = tid % 4;
           const double* Af = &s.A[0][0];
           double gl[4];
 #pragma unroll
@@ -470,10 +458,17 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
   }
 }
 
-__global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ mom,
-                                                              EmState* __restrict__ st, DevParams dp,
-                                                              double* __restrict__ trace) {
+// One CTA per pair: its Newton M step, sigma^2 update, trace and E-step constants.
+__global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ mom_all,
+                                                              EmState* __restrict__ st_all, DevParams dp,
+                                                              double* __restrict__ trace_all, int trace_iters,
+                                                              int* __restrict__ done_count, int P) {
   __shared__ Shared s;
+  if (*done_count >= P) return;
+  const int pair = blockIdx.x;
+  EmState* st = st_all + pair;
+  const double* mom = mom_all + static_cast<size_t>(pair) * kGlob;
+  double* trace = trace_all ? trace_all + static_cast<size_t>(pair) * trace_iters * 8 : nullptr;
   if (st->done) return;
   const int tid = threadIdx.x;
   load_model(s, mom);
@@ -487,6 +482,7 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     if (tid == 0) {
       st->numeric_fail = 1;
       st->done = 1;
+      atomicAdd(done_count, 1);
     }
     return;
   }
@@ -539,7 +535,10 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     tr[7] = mom[74];
   }
   st->iter = it + 1;
-  if (done_sh || (dp.tol > 0.0 && motion < dp.tol)) st->done = 1;
+  if (done_sh || (dp.tol > 0.0 && motion < dp.tol)) {
+    st->done = 1;
+    atomicAdd(done_count, 1);
+  }
   // E-step constants (the rotation/translation copies were written above)
   const float s2f = static_cast<float>(s2);
   const float lg = log2f(6.2831853f * s2f);
@@ -598,8 +597,9 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
 
 }  // namespace
 
-cudaError_t launch_mstep(const double* mom, EmState* st, const DevParams& dp, double* trace, cudaStream_t s) {
-  mstep_em_kernel<<<1, kMThreads, 0, s>>>(mom, st, dp, trace);
+cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* mom, const DevParams& dp, double* trace,
+                         int trace_iters, cudaStream_t s) {
+  mstep_em_kernel<<<p.g.P, kMThreads, 0, s>>>(mom, d.st, dp, trace, trace_iters, d.done_count, p.g.P);
   return cudaGetLastError();
 }
 

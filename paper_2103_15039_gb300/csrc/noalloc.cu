@@ -48,7 +48,9 @@ size_t align256(size_t n) { return (n + 255) & ~static_cast<size_t>(255); }
 struct Carve {
   lsg::EmState* st;
   int* status;
-  int* table;
+  int* done_count;
+  int* tab;
+  long long* off64;
   double* red;
   double* rows;
   double* mom;
@@ -59,27 +61,29 @@ struct Carve {
   float* part;
 };
 
-bool carve(unsigned char* base, const lsg::EstepPlan& p, int64_t N, int nrows, Carve* c) {
+bool carve(unsigned char* base, const lsg::BatchPlan& p, Carve* c) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     unsigned char* q = base + off;
     off += align256(bytes);
     return q;
   };
-  const size_t n_pad = static_cast<size_t>(p.num_blocks) * p.SB;
-  const size_t m_pad = static_cast<size_t>(p.num_tiles) * lsg::kTile;
+  const lsg::Geo& g = p.g;
+  const size_t n_pad = static_cast<size_t>(g.B) * g.SB;
+  const size_t m_pad = static_cast<size_t>(g.T) * lsg::kTile;
   c->st = reinterpret_cast<lsg::EmState*>(take(sizeof(lsg::EmState)));
   c->status = reinterpret_cast<int*>(take(sizeof(int)));
-  c->table = reinterpret_cast<int*>(take(sizeof(int) * p.table.size()));
-  c->red = reinterpret_cast<double*>(take(sizeof(double) * 1024 * 20));
-  c->rows = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(nrows) * lsg::kGlob));
-  c->mom = reinterpret_cast<double*>(take(sizeof(double) * 128));
+  c->done_count = reinterpret_cast<int*>(take(sizeof(int)));
+  c->tab = reinterpret_cast<int*>(take(sizeof(int) * p.tab.size()));
+  c->off64 = reinterpret_cast<long long*>(take(sizeof(long long) * p.off64.size()));
+  c->red = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(lsg::stats_chunks(g)) * 20));
+  c->rows = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(g.combine_ctas) * lsg::kGlob));
+  c->mom = reinterpret_cast<double*>(take(sizeof(double) * lsg::kGlob));
   c->xs = reinterpret_cast<float4*>(take(sizeof(float4) * n_pad));
   c->rec = reinterpret_cast<float*>(take(sizeof(float) * m_pad * lsg::kPlanes));
   c->kap = reinterpret_cast<float*>(take(sizeof(float) * n_pad));
   c->gam = reinterpret_cast<float*>(take(sizeof(float) * n_pad));
-  c->part = reinterpret_cast<float*>(take(sizeof(float) * lsg::estep_partial_floats(p)));
-  (void)N;
+  c->part = reinterpret_cast<float*>(take(sizeof(float) * lsg::estep_partial_floats(g)));
   return off <= kArenaBytes;
 }
 
@@ -135,20 +139,27 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
     cudaGetLastError();
     return LSGCPD_ECUDA;
   }
-  const lsg::EstepPlan plan = lsg::plan_estep(N, M, sms, 0);
-  const int nrows = lsg::combine_rows(N, sms);
+  const lsg::BatchPlan plan = lsg::plan_batch({N}, {M}, sms, 0);
   Carve c;
-  if (!carve(base, plan, N, nrows, &c)) return LSGCPD_ENOMEM;  // cannot happen within the stated limits
+  if (!carve(base, plan, &c)) return LSGCPD_ENOMEM;  // cannot happen within the stated limits
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int64_t n_pad = static_cast<int64_t>(plan.num_blocks) * plan.SB;
-  // the arena keeps the previous call's contents: the status word must start at zero,
-  // everything else below is written before it is read
+  const lsg::Dev d{c.tab, c.off64, c.st, c.done_count};
+  // the arena keeps the previous call's contents: the status word and the
+  // finished-pair count must start at zero, everything else below is written
+  // before it is read
   cudaError_t e = cudaMemsetAsync(c.status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c.done_count, 0, sizeof(int), s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c.table, plan.table.data(), sizeof(int) * plan.table.size(), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = lsg::launch_center_only(X, N, Y, M, c.red, c.st, c.xs, n_pad, s);
+    e = cudaMemcpyAsync(c.tab, plan.tab.data(), sizeof(int) * plan.tab.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c.off64, plan.off64.data(), sizeof(long long) * plan.off64.size(), cudaMemcpyHostToDevice,
+                        s);
+  lsg::DevParams dp{};
+  dp.w = p->w;
+  dp.volume = volume;
+  if (e == cudaSuccess) e = lsg::launch_init(plan, d, X, Y, dp, false, c.red, c.xs, s);
   if (e == cudaSuccess) e = lsg::launch_estep_constants(c.st, sigma2, p->w, volume, R, t, s);
-  if (e == cudaSuccess) e = lsg::launch_pack(Y, normals, alpha, M, p->include_alpha_norm, c.st, c.rec, plan.num_tiles, s);
+  if (e == cudaSuccess) e = lsg::launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c.rec, s);
   // fixed shift unless the outlier term is absent or a term could overflow FP32
   int mode = 1;
   if (p->w > 0.0) {
@@ -156,13 +167,11 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
     const double l_max = -log2(static_cast<double>(M)) + (p->include_alpha_norm ? 12.0 : 0.0);
     mode = (l_max - L + log2(static_cast<double>(M)) + 12.0 < 126.0) ? 0 : 1;
   }
-  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, c.xs, c.rec, c.st, N, c.kap, c.gam, s);
+  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, c.kap, c.gam, s);
+  if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode ? c.kap : nullptr, c.part, c.status, s);
   if (e == cudaSuccess)
-    e = lsg::launch_estep(plan, c.xs, c.rec, c.st, mode ? c.kap : nullptr, c.part, c.table, c.status, s);
-  if (e == cudaSuccess)
-    e = lsg::launch_combine(plan, c.xs, N, c.part, c.table, c.st, mode ? c.kap : nullptr, mode ? c.gam : nullptr,
-                            c.rows, nrows, per_n, s);
-  if (e == cudaSuccess) e = lsg::launch_final_reduce(c.rows, nrows, c.mom, nullptr, s);
+    e = lsg::launch_combine(plan, d, c.xs, c.part, mode ? c.kap : nullptr, mode ? c.gam : nullptr, c.rows, per_n, s);
+  if (e == cudaSuccess) e = lsg::launch_final_reduce(plan, d, c.rows, c.mom, s);
   double mom[LSGCPD_MOMENTS];
   double mu[3];
   int status = 0;

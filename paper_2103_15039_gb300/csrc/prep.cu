@@ -21,7 +21,7 @@ namespace lsg {
 namespace {
 
 constexpr int kStatThreads = 256;
-constexpr int kStatBlocksMax = 1024;
+constexpr int kStatChunk = kStatThreads * 16;  // points per statistics CTA
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -60,47 +60,61 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* out_r
   }
 }
 
-// Pass 1: sum x (3), sum y (3), min y (3), max y (3).
-__global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __restrict__ X, long long N,
-                                                                 const float* __restrict__ Y, long long M,
+// Pass 1 (per pair, per chunk of kStatChunk points): sum x (3), sum y (3),
+// min y (3), max y (3).  grid = (chunks, P).
+__global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                                                 const long long* __restrict__ off64, int P,
                                                                  double* __restrict__ red) {
+  const int pair = blockIdx.y;
+  const long long n0 = off64[pair], N = off64[pair + 1] - n0;
+  const long long m0 = off64[P + 1 + pair], M = off64[P + 1 + pair + 1] - m0;
+  const long long c0 = static_cast<long long>(blockIdx.x) * kStatChunk;
+  if (c0 >= (N > M ? N : M)) return;
   double v[12];
   const int op[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2};
   for (int j = 0; j < 6; ++j) v[j] = 0.0;
   for (int j = 6; j < 9; ++j) v[j] = INFINITY;
   for (int j = 9; j < 12; ++j) v[j] = -INFINITY;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
-    v[0] += X[3 * i];
-    v[1] += X[3 * i + 1];
-    v[2] += X[3 * i + 2];
+  for (long long i = c0 + threadIdx.x; i < c0 + kStatChunk; i += kStatThreads) {
+    if (i < N) {
+      const float* x = X + 3 * (n0 + i);
+      v[0] += x[0];
+      v[1] += x[1];
+      v[2] += x[2];
+    }
+    if (i < M) {
+      const float* y = Y + 3 * (m0 + i);
+      const double a = y[0], b = y[1], c = y[2];
+      v[3] += a;
+      v[4] += b;
+      v[5] += c;
+      v[6] = fmin(v[6], a);
+      v[7] = fmin(v[7], b);
+      v[8] = fmin(v[8], c);
+      v[9] = fmax(v[9], a);
+      v[10] = fmax(v[10], b);
+      v[11] = fmax(v[11], c);
+    }
   }
-  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < M; i += stride) {
-    const double a = Y[3 * i], b = Y[3 * i + 1], c = Y[3 * i + 2];
-    v[3] += a;
-    v[4] += b;
-    v[5] += c;
-    v[6] = fmin(v[6], a);
-    v[7] = fmin(v[7], b);
-    v[8] = fmin(v[8], c);
-    v[9] = fmax(v[9], a);
-    v[10] = fmax(v[10], b);
-    v[11] = fmax(v[11], c);
-  }
-  block_reduce<12>(v, op, red + static_cast<size_t>(blockIdx.x) * 12);
+  block_reduce<12>(v, op, red + (static_cast<size_t>(pair) * gridDim.x + blockIdx.x) * 12);
 }
 
-// Finalise pass 1: centroids, V, diagonal and sigma^2 floor.  One warp per
-// reduced value (lanes over the partial rows), then thread 0 finishes.
-__global__ void finalize_raw_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
-                                    double volume, double floor_rel, EmState* __restrict__ st) {
+// Finalise pass 1 per pair (grid = P, one warp per value): centroids, V,
+// diagonal and sigma^2 floor.
+__global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, const long long* __restrict__ off64,
+                                    int P, double volume, double floor_rel, EmState* __restrict__ st_all) {
   __shared__ double v[12];
+  const int pair = blockIdx.x;
+  const long long N = off64[pair + 1] - off64[pair];
+  const long long M = off64[P + 1 + pair + 1] - off64[P + 1 + pair];
+  const long long big = N > M ? N : M;
+  const int nchunk = static_cast<int>((big + kStatChunk - 1) / kStatChunk);
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j < 12) {
     const int op = j < 6 ? 0 : (j < 9 ? 1 : 2);
     double x = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
-    for (int b = lane; b < nblk; b += 32) {
-      const double r = red[static_cast<size_t>(b) * 12 + j];
+    for (int b = lane; b < nchunk; b += 32) {
+      const double r = red[(static_cast<size_t>(pair) * chunks + b) * 12 + j];
       x = op == 0 ? x + r : (op == 1 ? fmin(x, r) : fmax(x, r));
     }
     x = op == 0 ? warp_sum_d(x) : (op == 1 ? warp_min_d(x) : warp_max_d(x));
@@ -108,6 +122,7 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int nblk, lo
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  EmState* st = st_all + pair;
   for (int c = 0; c < 3; ++c) {
     st->mu_x[c] = v[c] / static_cast<double>(N);
     st->mu_y[c] = v[3 + c] / static_cast<double>(M);
@@ -125,67 +140,90 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int nblk, lo
   st->sigma2_floor = floor_rel * diag * diag;
 }
 
-// Pass 2: centred FP32 copies (sources as float4, padded with zeros up to n_pad)
-// and sums of the centred clouds: sum xc (3), sum |xc|^2, sum yc (3), sum |yc|^2.
-__global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __restrict__ X, long long N,
-                                                              const float* __restrict__ Y, long long M,
-                                                              const EmState* __restrict__ st,
-                                                              float4* __restrict__ xs, long long n_pad,
-                                                              double* __restrict__ red) {
+// Pass 2 (grid = (chunks, P)): centred FP32 sources as float4 (zero padding up
+// to the pair's whole source blocks) and sums of the centred clouds:
+// sum xc (3), sum |xc|^2, sum yc (3), sum |yc|^2.
+__global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                                              const long long* __restrict__ off64,
+                                                              const int* __restrict__ tab, Geo g,
+                                                              const EmState* __restrict__ st_all,
+                                                              float4* __restrict__ xs, double* __restrict__ red) {
+  const int pair = blockIdx.y;
+  const int P = g.P;
+  const long long n0 = off64[pair], N = off64[pair + 1] - n0;
+  const long long m0 = off64[P + 1 + pair], M = off64[P + 1 + pair + 1] - m0;
+  const long long xb = static_cast<long long>(tab[g.o_blk_off + pair]) * g.SB;
+  const long long npad = static_cast<long long>(tab[g.o_blk_off + pair + 1]) * g.SB - xb;
+  const long long big = npad > M ? npad : M;
+  const long long c0 = static_cast<long long>(blockIdx.x) * kStatChunk;
+  if (c0 >= big) return;
+  const EmState* st = st_all + pair;
   double v[8];
   const int op[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int j = 0; j < 8; ++j) v[j] = 0.0;
   const double mx0 = st->mu_x[0], mx1 = st->mu_x[1], mx2 = st->mu_x[2];
   const double my0 = st->mu_y[0], my1 = st->mu_y[1], my2 = st->mu_y[2];
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
-    if (i < N) {
-      const double a = X[3 * i] - mx0, b = X[3 * i + 1] - mx1, c = X[3 * i + 2] - mx2;
-      const float fa = static_cast<float>(a), fb = static_cast<float>(b), fc = static_cast<float>(c);
-      xs[i] = make_float4(fa, fb, fc, 0.f);
-      v[0] += fa;
-      v[1] += fb;
-      v[2] += fc;
-      v[3] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
-    } else {
-      xs[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = c0 + threadIdx.x; i < c0 + kStatChunk; i += kStatThreads) {
+    if (i < npad) {
+      if (i < N) {
+        const float* x = X + 3 * (n0 + i);
+        const float fa = static_cast<float>(x[0] - mx0), fb = static_cast<float>(x[1] - mx1),
+                    fc = static_cast<float>(x[2] - mx2);
+        xs[xb + i] = make_float4(fa, fb, fc, 0.f);
+        v[0] += fa;
+        v[1] += fb;
+        v[2] += fc;
+        v[3] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
+      } else {
+        xs[xb + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (i < M) {
+      const float* y = Y + 3 * (m0 + i);
+      const float fa = static_cast<float>(y[0] - my0), fb = static_cast<float>(y[1] - my1),
+                  fc = static_cast<float>(y[2] - my2);
+      v[4] += fa;
+      v[5] += fb;
+      v[6] += fc;
+      v[7] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
     }
   }
-  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < M; i += stride) {
-    const float fa = static_cast<float>(Y[3 * i] - my0);
-    const float fb = static_cast<float>(Y[3 * i + 1] - my1);
-    const float fc = static_cast<float>(Y[3 * i + 2] - my2);
-    v[4] += fa;
-    v[5] += fb;
-    v[6] += fc;
-    v[7] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
-  }
-  block_reduce<8>(v, op, red + static_cast<size_t>(blockIdx.x) * 8);
+  block_reduce<8>(v, op, red + (static_cast<size_t>(pair) * gridDim.x + blockIdx.x) * 8);
 }
 
-// Finalise pass 2: initial pose in the centred frame, sigma^2_0, E-step constants.
-// t_c = R0 mu_x + t0 - mu_y;  with z = R0 xc + t_c:
+// Finalise pass 2 per pair (grid = P): initial pose in the centred frame,
+// sigma^2_0, E-step constants.  t_c = R0 mu_x + t0 - mu_y;  with z = R0 xc + t_c:
 //   sum z = R0 sum xc + N t_c,  sum |z|^2 = sum |xc|^2 + 2 t_c . (R0 sum xc) + N |t_c|^2,
 //   sigma^2_0 = (M sum|z|^2 + N sum|yc|^2 - 2 sum z . sum yc) / (3 N M).
-__global__ void finalize_init_kernel(const double* __restrict__ red, int nblk, long long N, long long M,
-                                     DevParams dp, EmState* __restrict__ st) {
+__global__ void finalize_init_kernel(const double* __restrict__ red, int chunks, const long long* __restrict__ off64,
+                                     const int* __restrict__ tab, Geo g, DevParams dp, EmState* __restrict__ st_all,
+                                     int* __restrict__ done_count) {
   __shared__ double v[8];
+  const int pair = blockIdx.x;
+  const int P = g.P;
+  const long long N = off64[pair + 1] - off64[pair];
+  const long long M = off64[P + 1 + pair + 1] - off64[P + 1 + pair];
+  const long long npad = static_cast<long long>(tab[g.o_blk_off + pair + 1] - tab[g.o_blk_off + pair]) * g.SB;
+  const long long big = npad > M ? npad : M;
+  const int nchunk = static_cast<int>((big + kStatChunk - 1) / kStatChunk);
   {
     const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (j < 8) {
       double x = 0.0;
-      for (int b = lane; b < nblk; b += 32) x += red[static_cast<size_t>(b) * 8 + j];
+      for (int b = lane; b < nchunk; b += 32) x += red[(static_cast<size_t>(pair) * chunks + b) * 8 + j];
       x = warp_sum_d(x);
       if (lane == 0) v[j] = x;
     }
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
+  if (pair == 0) *done_count = 0;
+  EmState* st = st_all + pair;
   const double* R = dp.init_R;
   double tc[3], Rsx[3];
   for (int i = 0; i < 3; ++i) {
-    tc[i] = R[3 * i] * st->mu_x[0] + R[3 * i + 1] * st->mu_x[1] + R[3 * i + 2] * st->mu_x[2] +
-            dp.init_t[i] - st->mu_y[i];
+    tc[i] = R[3 * i] * st->mu_x[0] + R[3 * i + 1] * st->mu_x[1] + R[3 * i + 2] * st->mu_x[2] + dp.init_t[i] -
+            st->mu_y[i];
     Rsx[i] = R[3 * i] * v[0] + R[3 * i + 1] * v[1] + R[3 * i + 2] * v[2];
   }
   const double Nd = static_cast<double>(N), Md = static_cast<double>(M);
@@ -246,26 +284,34 @@ __device__ __forceinline__ void knn_insert(float (&bd)[KMAX], int (&bi)[KMAX], f
 // Two queries per thread (q and q + kKnnThreads), packed FP32x2 distances:
 // with the candidate stored negated, p + (-c) is exactly p - c, and
 // fma(dz, dz, fma(dy, dy, dx * dx)) per half is the scalar formula.
+// grid = (query blocks of the largest pair, P, splits); candidates are the
+// split's share of the query's own pair.
 // KFIX > 0: k == KFIX is a compile-time constant (lists stay in registers);
 // KFIX == 0: runtime k <= KMAX.
 template <int KMAX, int KFIX>
-__global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* __restrict__ y4, long long M,
-                                                                  int k_rt, int splits,
+__global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* __restrict__ y4,
+                                                                  const long long* __restrict__ off64, int P,
+                                                                  long long Mtot, int k_rt, int splits,
                                                                   float* __restrict__ part_d,
                                                                   int* __restrict__ part_i) {
   const int k = KFIX > 0 ? KFIX : k_rt;
   __shared__ float4 cxy[kKnnTile];  // (-x, -x, -y, -y)
   __shared__ float2 cz[kKnnTile];   // (-z, -z)
-  const long long q0 = static_cast<long long>(blockIdx.x) * (2 * kKnnThreads) + threadIdx.x;
+  const int pair = blockIdx.y;
+  const long long m0 = off64[P + 1 + pair];
+  const long long M = off64[P + 1 + pair + 1] - m0;
+  const long long qb = static_cast<long long>(blockIdx.x) * (2 * kKnnThreads);
+  if (qb >= M) return;
+  const long long q0 = qb + threadIdx.x;
   const long long q1 = q0 + kKnnThreads;
-  const int split = blockIdx.y;
+  const int split = blockIdx.z;
   const long long per = (M + splits - 1) / splits;
   const long long c_lo = split * per;
   long long c_hi = c_lo + per;
   if (c_hi > M) c_hi = M;
   const bool v0 = q0 < M, v1 = q1 < M;
-  const float4 p0 = v0 ? y4[q0] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 p1 = v1 ? y4[q1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 p0 = v0 ? y4[m0 + q0] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 p1 = v1 ? y4[m0 + q1] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float2 px = make_float2(p0.x, p1.x), py = make_float2(p0.y, p1.y), pz = make_float2(p0.z, p1.z);
   float bd0[KMAX], bd1[KMAX];
   int bi0[KMAX], bi1[KMAX];
@@ -279,7 +325,7 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
     const int cnt = static_cast<int>((c_hi - base) < kKnnTile ? (c_hi - base) : kKnnTile);
     __syncthreads();
     for (int j = threadIdx.x; j < cnt; j += kKnnThreads) {
-      const float4 c = y4[base + j];
+      const float4 c = y4[m0 + base + j];
       cxy[j] = make_float4(-c.x, -c.x, -c.y, -c.y);
       cz[j] = make_float2(-c.z, -c.z);
     }
@@ -296,8 +342,8 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
     }
   }
   if (v0) {
-    float* od = part_d + (static_cast<size_t>(split) * M + q0) * k;
-    int* oi = part_i + (static_cast<size_t>(split) * M + q0) * k;
+    float* od = part_d + (static_cast<size_t>(split) * Mtot + m0 + q0) * k;
+    int* oi = part_i + (static_cast<size_t>(split) * Mtot + m0 + q0) * k;
 #pragma unroll
     for (int s = 0; s < KMAX; ++s)
       if (s < k) {
@@ -306,8 +352,8 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
       }
   }
   if (v1) {
-    float* od = part_d + (static_cast<size_t>(split) * M + q1) * k;
-    int* oi = part_i + (static_cast<size_t>(split) * M + q1) * k;
+    float* od = part_d + (static_cast<size_t>(split) * Mtot + m0 + q1) * k;
+    int* oi = part_i + (static_cast<size_t>(split) * Mtot + m0 + q1) * k;
 #pragma unroll
     for (int s = 0; s < KMAX; ++s)
       if (s < k) {
@@ -318,10 +364,10 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
 }
 
 // Merge the sorted partial lists of every split by (distance, index).
-__global__ void knn_merge_kernel(const float* __restrict__ part_d, const int* __restrict__ part_i,
-                                 long long M, int k, int splits, int* __restrict__ idx) {
+__global__ void knn_merge_kernel(const float* __restrict__ part_d, const int* __restrict__ part_i, long long Mtot,
+                                 int k, int splits, int* __restrict__ idx) {
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= M) return;
+  if (q >= Mtot) return;
   int head[64];
   for (int s = 0; s < splits; ++s) head[s] = 0;
   for (int r = 0; r < k; ++r) {
@@ -330,7 +376,7 @@ __global__ void knn_merge_kernel(const float* __restrict__ part_d, const int* __
     int bi = 0x7fffffff;
     for (int s = 0; s < splits; ++s) {
       if (head[s] >= k) continue;
-      const size_t o = (static_cast<size_t>(s) * M + q) * k + head[s];
+      const size_t o = (static_cast<size_t>(s) * Mtot + q) * k + head[s];
       const float d = part_d[o];
       const int i = part_i[o];
       if (d < bd || (d == bd && i < bi)) {
@@ -397,31 +443,41 @@ __device__ __forceinline__ void write_record(float* rec, long long m, float ny0,
   for (int p = 0; p < kPlanes; ++p) r[p * kTile] = v[p];
 }
 
-__device__ __forceinline__ void pack_target(float* rec, long long m, const float* Y, const EmState* st,
+__device__ __forceinline__ void pack_target(float* rec, long long slot, const float* y, const EmState* st,
                                             double nx, double ny, double nz, double alpha, double log2_pi,
                                             int alpha_norm) {
   const double sa = sqrt(alpha > 0.0 ? alpha : 0.0);
   const double l = log2_pi + (alpha_norm ? 0.5 * log2(1.0 + alpha) : 0.0);
-  write_record(rec, m, static_cast<float>(-(Y[3 * m] - st->mu_y[0])),
-               static_cast<float>(-(Y[3 * m + 1] - st->mu_y[1])),
-               static_cast<float>(-(Y[3 * m + 2] - st->mu_y[2])), static_cast<float>(sa * nx),
-               static_cast<float>(sa * ny), static_cast<float>(sa * nz), static_cast<float>(l));
+  write_record(rec, slot, static_cast<float>(-(y[0] - st->mu_y[0])), static_cast<float>(-(y[1] - st->mu_y[1])),
+               static_cast<float>(-(y[2] - st->mu_y[2])), static_cast<float>(sa * nx), static_cast<float>(sa * ny),
+               static_cast<float>(sa * nz), static_cast<float>(l));
 }
 
-__global__ void geometry_kernel(const float* __restrict__ Y, long long M, const int* __restrict__ idx, int k,
-                                double alpha_max, double lambda, int alpha_norm,
-                                const EmState* __restrict__ st, float* __restrict__ rec, long long m_pad,
-                                float* __restrict__ normals, float* __restrict__ kappa,
-                                float* __restrict__ alpha_out) {
-  const long long m = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (m >= m_pad) return;
+// grid = (largest tile count, P), kTile threads: target m = tile * kTile + tid of
+// the pair; its record slot is (tile_off[pair] + tile) * kTile + tid.
+__global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict__ Y,
+                                                         const long long* __restrict__ off64,
+                                                         const int* __restrict__ tab, Geo g,
+                                                         const int* __restrict__ idx, int k, double alpha_max,
+                                                         double lambda, int alpha_norm,
+                                                         const EmState* __restrict__ st_all,
+                                                         float* __restrict__ rec, float* __restrict__ normals,
+                                                         float* __restrict__ kappa, float* __restrict__ alpha_out) {
+  const int pair = blockIdx.y;
+  const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
+  if (static_cast<int>(blockIdx.x) >= t1 - t0) return;
+  const long long m0 = off64[g.P + 1 + pair];
+  const long long M = off64[g.P + 1 + pair + 1] - m0;
+  const long long m = static_cast<long long>(blockIdx.x) * kTile + threadIdx.x;
+  const long long slot = static_cast<long long>(t0 + blockIdx.x) * kTile + threadIdx.x;
   if (m >= M) {
-    write_record(rec, m, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    write_record(rec, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
     return;
   }
+  const long long gm = m0 + m;
   double mean[3] = {0.0, 0.0, 0.0};
   for (int j = 0; j < k; ++j) {
-    const long long q = idx[m * k + j];
+    const long long q = m0 + idx[gm * k + j];
     mean[0] += Y[3 * q];
     mean[1] += Y[3 * q + 1];
     mean[2] += Y[3 * q + 2];
@@ -429,7 +485,7 @@ __global__ void geometry_kernel(const float* __restrict__ Y, long long M, const 
   for (int c = 0; c < 3; ++c) mean[c] /= k;
   double C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int j = 0; j < k; ++j) {
-    const long long q = idx[m * k + j];
+    const long long q = m0 + idx[gm * k + j];
     const double d[3] = {Y[3 * q] - mean[0], Y[3 * q + 1] - mean[1], Y[3 * q + 2] - mean[2]};
     for (int r = 0; r < 3; ++r)
       for (int c = 0; c < 3; ++c) C[r][c] += d[r] * d[c] / k;
@@ -455,101 +511,107 @@ __global__ void geometry_kernel(const float* __restrict__ Y, long long M, const 
   }
   double a = kap > 0.0 ? alpha_max * tanh(0.5 * lambda * (1.0 / kap - 3.0)) : alpha_max;
   if (a < 0.0) a = 0.0;
-  pack_target(rec, m, Y, st, n0, n1, n2, a, -log2(static_cast<double>(M)), alpha_norm);
+  pack_target(rec, slot, Y + 3 * gm, st_all + pair, n0, n1, n2, a, -log2(static_cast<double>(M)), alpha_norm);
   if (normals) {
-    normals[3 * m] = static_cast<float>(n0);
-    normals[3 * m + 1] = static_cast<float>(n1);
-    normals[3 * m + 2] = static_cast<float>(n2);
+    normals[3 * gm] = static_cast<float>(n0);
+    normals[3 * gm + 1] = static_cast<float>(n1);
+    normals[3 * gm + 2] = static_cast<float>(n2);
   }
-  if (kappa) kappa[m] = static_cast<float>(kap);
-  if (alpha_out) alpha_out[m] = static_cast<float>(a);
+  if (kappa) kappa[gm] = static_cast<float>(kap);
+  if (alpha_out) alpha_out[gm] = static_cast<float>(a);
 }
 
-__global__ void pack_kernel(const float* __restrict__ Y, const float* __restrict__ normals,
-                            const float* __restrict__ alpha, long long M, int alpha_norm,
-                            const EmState* __restrict__ st, float* __restrict__ rec, long long m_pad) {
-  const long long m = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (m >= m_pad) return;
+__global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y, const long long* __restrict__ off64,
+                                                     const int* __restrict__ tab, Geo g,
+                                                     const float* __restrict__ normals, const float* __restrict__ alpha,
+                                                     int alpha_norm, const EmState* __restrict__ st_all,
+                                                     float* __restrict__ rec) {
+  const int pair = blockIdx.y;
+  const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
+  if (static_cast<int>(blockIdx.x) >= t1 - t0) return;
+  const long long m0 = off64[g.P + 1 + pair];
+  const long long M = off64[g.P + 1 + pair + 1] - m0;
+  const long long m = static_cast<long long>(blockIdx.x) * kTile + threadIdx.x;
+  const long long slot = static_cast<long long>(t0 + blockIdx.x) * kTile + threadIdx.x;
   if (m >= M) {
-    write_record(rec, m, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    write_record(rec, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
     return;
   }
-  pack_target(rec, m, Y, st, normals[3 * m], normals[3 * m + 1], normals[3 * m + 2], alpha[m],
-              -log2(static_cast<double>(M)), alpha_norm);
+  const long long gm = m0 + m;
+  pack_target(rec, slot, Y + 3 * gm, st_all + pair, normals[3 * gm], normals[3 * gm + 1], normals[3 * gm + 2],
+              alpha[gm], -log2(static_cast<double>(M)), alpha_norm);
 }
 
 }  // namespace
 
-int stats_blocks(int64_t n) {
-  const long long b = (n + kStatThreads - 1) / kStatThreads;
-  return static_cast<int>(b < kStatBlocksMax ? (b > 0 ? b : 1) : kStatBlocksMax);
+int stats_chunks(const Geo& g) {
+  const long long big_n = static_cast<long long>(g.max_blocks) * g.SB;
+  const long long big = big_n > g.max_m ? big_n : g.max_m;
+  return static_cast<int>((big + kStatChunk - 1) / kStatChunk);
 }
 
-cudaError_t launch_center_only(const float* X, int64_t N, const float* Y, int64_t M, double* red,
-                               EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
-  const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : M);
-  raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
-  finalize_raw_kernel<<<1, 12 * 32, 0, s>>>(red, nb, N, M, 0.0, 0.0, st);
-  center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red + static_cast<size_t>(kStatBlocksMax) * 12);
+cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const DevParams& dp,
+                        bool full, double* red, float4* xs, cudaStream_t s) {
+  const Geo& g = p.g;
+  const int chunks = stats_chunks(g);
+  dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(g.P));
+  raw_stats_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, d.off64, g.P, red);
+  finalize_raw_kernel<<<g.P, 12 * 32, 0, s>>>(red, chunks, d.off64, g.P, full ? dp.volume : 0.0,
+                                              full ? dp.sigma2_floor_rel : 0.0, d.st);
+  double* red2 = red + static_cast<size_t>(g.P) * chunks * 12;
+  center_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, d.off64, d.tab, g, d.st, xs, red2);
+  if (full) finalize_init_kernel<<<g.P, 8 * 32, 0, s>>>(red2, chunks, d.off64, d.tab, g, dp, d.st, d.done_count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_init(const float* X, int64_t N, const float* Y, int64_t M, const DevParams& dp,
-                        double* red, EmState* st, float4* xs, int64_t n_pad, cudaStream_t s) {
-  const int nb = stats_blocks(N > M ? (n_pad > N ? n_pad : N) : (n_pad > M ? n_pad : M));
-  raw_stats_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, red);
-  finalize_raw_kernel<<<1, 12 * 32, 0, s>>>(red, nb, N, M, dp.volume, dp.sigma2_floor_rel, st);
-  double* red2 = red + static_cast<size_t>(kStatBlocksMax) * 12;
-  center_kernel<<<nb, kStatThreads, 0, s>>>(X, N, Y, M, st, xs, n_pad, red2);
-  finalize_init_kernel<<<1, 8 * 32, 0, s>>>(red2, nb, N, M, dp, st);
-  return cudaGetLastError();
-}
-
-int knn_splits(int64_t M, int num_sms) {
-  const long long qblocks = (M + 2 * kKnnThreads - 1) / (2 * kKnnThreads);
+int knn_splits(const Geo& g, int num_sms) {
+  long long qblocks = 0;  // total query blocks over the batch is approximated by P x the largest pair
+  qblocks = static_cast<long long>(g.P) * ((g.max_m + 2 * kKnnThreads - 1) / (2 * kKnnThreads));
   long long sp = (4LL * num_sms + qblocks - 1) / qblocks;
   if (sp < 1) sp = 1;
   if (sp > 32) sp = 32;
-  // at least 64 candidates per split
-  while (sp > 1 && M / sp < 64) --sp;
+  // at least 64 candidates per split in the largest pair
+  while (sp > 1 && g.max_m / sp < 64) --sp;
   return static_cast<int>(sp);
 }
 
-cudaError_t launch_knn(const float* Y, int64_t M, int k, float4* y4, float* part_d, int* part_i,
-                       int* idx_out, int splits, cudaStream_t s) {
-  to_float4_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, s>>>(Y, M, y4);
-  dim3 grid(static_cast<unsigned>((M + 2 * kKnnThreads - 1) / (2 * kKnnThreads)), static_cast<unsigned>(splits));
+cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, int splits, float4* y4,
+                       float* part_d, int* part_i, int* idx_out, cudaStream_t s) {
+  const Geo& g = p.g;
+  const long long Mtot = p.off64[2 * g.P + 1];
+  to_float4_kernel<<<static_cast<unsigned>((Mtot + 255) / 256), 256, 0, s>>>(Y, Mtot, y4);
+  dim3 grid(static_cast<unsigned>((g.max_m + 2 * kKnnThreads - 1) / (2 * kKnnThreads)), static_cast<unsigned>(g.P),
+            static_cast<unsigned>(splits));
   switch (k) {
 #define LSG_KNN_CASE(K) \
   case K:               \
-    knn_partial_kernel<K, K><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i); \
+    knn_partial_kernel<K, K><<<grid, kKnnThreads, 0, s>>>(y4, d.off64, g.P, Mtot, k, splits, part_d, part_i); \
     break;
     LSG_KNN_CASE(1) LSG_KNN_CASE(2) LSG_KNN_CASE(3) LSG_KNN_CASE(4) LSG_KNN_CASE(5) LSG_KNN_CASE(6)
     LSG_KNN_CASE(7) LSG_KNN_CASE(8) LSG_KNN_CASE(9) LSG_KNN_CASE(10) LSG_KNN_CASE(11) LSG_KNN_CASE(12)
     LSG_KNN_CASE(13) LSG_KNN_CASE(14) LSG_KNN_CASE(15) LSG_KNN_CASE(16)
 #undef LSG_KNN_CASE
     default:
-      knn_partial_kernel<32, 0><<<grid, kKnnThreads, 0, s>>>(y4, M, k, splits, part_d, part_i);
+      knn_partial_kernel<32, 0><<<grid, kKnnThreads, 0, s>>>(y4, d.off64, g.P, Mtot, k, splits, part_d, part_i);
   }
-  knn_merge_kernel<<<static_cast<unsigned>((M + 127) / 128), 128, 0, s>>>(part_d, part_i, M, k, splits,
-                                                                         idx_out);
+  knn_merge_kernel<<<static_cast<unsigned>((Mtot + 127) / 128), 128, 0, s>>>(part_d, part_i, Mtot, k, splits,
+                                                                            idx_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_geometry(const float* Y, int64_t M, const int* idx, int k, double alpha_max,
-                            double lambda, int alpha_norm, const EmState* st, float* rec, int num_tiles,
-                            float* normals, float* kappa, float* alpha, cudaStream_t s) {
-  const long long m_pad = static_cast<long long>(num_tiles) * kTile;
-  geometry_kernel<<<static_cast<unsigned>((m_pad + 127) / 128), 128, 0, s>>>(
-      Y, M, idx, k, alpha_max, lambda, alpha_norm, st, rec, m_pad, normals, kappa, alpha);
+cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
+                            double alpha_max, double lambda, int alpha_norm, float* rec, float* normals,
+                            float* kappa, float* alpha, cudaStream_t s) {
+  dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
+  geometry_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, idx, k, alpha_max, lambda, alpha_norm, d.st, rec,
+                                         normals, kappa, alpha);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const float* Y, const float* normals, const float* alpha, int64_t M, int alpha_norm,
-                        const EmState* st, float* rec, int num_tiles, cudaStream_t s) {
-  const long long m_pad = static_cast<long long>(num_tiles) * kTile;
-  pack_kernel<<<static_cast<unsigned>((m_pad + 127) / 128), 128, 0, s>>>(Y, normals, alpha, M, alpha_norm,
-                                                                         st, rec, m_pad);
+cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals, const float* alpha,
+                        int alpha_norm, float* rec, cudaStream_t s) {
+  dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
+  pack_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, normals, alpha, alpha_norm, d.st, rec);
   return cudaGetLastError();
 }
 
