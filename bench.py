@@ -12,7 +12,13 @@ pinned host inputs (H2D inside the call, result read back to the host).
 The roofline object reports the hot E-step kernel, timed live with CUDA events
 on the stream it is launched on, against the FP32-pipe peak (ALU bound).
 
+With --workload batch256 a step is instead one batched registration of 256
+independent pairs with N, M log-uniform in [500, 20,000] (one launch per stage
+for the whole batch); the line then also carries the same 256 pairs registered
+one after another through lsgcpd_register (the plain per-pair form).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload rgbd20k|batch256]
 Under torchrun every rank registers its own independent pair (weak scaling,
 no collective on the data path); rank 0 prints one JSON line.
 """
@@ -49,6 +55,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["rgbd20k", "batch256"], default="rgbd20k")
     return ap.parse_args()
 
 
@@ -64,6 +71,19 @@ def workload(rank):
     seed = synth.SEED_BASE + 2 + 1000 * rank
     c = synth.rgbd_room_pair(seed=seed)
     return c, seed
+
+
+def batch_workload(rank):
+    import numpy as np
+
+    from paper_2103_15039_gb300 import synth
+    seed = synth.SEED_BASE + 4 + 1000 * rank
+    pairs = synth.batch_pairs(seed=seed)
+    X = np.concatenate([q["X"] for q in pairs]).astype(np.float32)
+    Y = np.concatenate([q["Y"] for q in pairs]).astype(np.float32)
+    n_off = np.concatenate([[0], np.cumsum([len(q["X"]) for q in pairs])]).astype(np.int64)
+    m_off = np.concatenate([[0], np.cumsum([len(q["Y"]) for q in pairs])]).astype(np.int64)
+    return pairs, X, n_off, Y, m_off, seed
 
 
 def config_obj(c, seed, iters, n_gpus):
@@ -307,6 +327,144 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """A step = one lsgcpd_register_batch call over 256 uneven pairs."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_15039_gb300 import binding
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pairs, X, n_off, Y, m_off, seed = batch_workload(rank)
+    P = len(pairs)
+    Ns, Ms = np.diff(n_off), np.diff(m_off)
+    nm = (Ns * Ms).astype(np.float64)
+    iters = args.iters
+    ctx = binding.Context(local, int(Ns.max()), int(Ms.max()))
+    p = binding.default_params(max_iters=iters)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    Xh, Yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx.set_timing(True)
+    for _ in range(max(args.warmup, 0)):
+        got = ctx.register_batch(Xd, n_off, Yd, m_off, p)
+        ctx.register_batch(Xh, n_off, Yh, m_off, p)
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms, estep_ms, launches = [], [], 0
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = ctx.register_batch(Xd, n_off, Yd, m_off, p)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        tm = ctx.last_timing()
+        estep_ms.append(tm["ms_estep"])
+        launches += tm["launches"]
+    barrier()
+    clk = clocks.stop()
+    iters_run = int(got["iters"].max())
+    pairs_per_step = float((got["iters"].astype(np.float64) * nm).sum())
+
+    e2e_s = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.register_batch(Xh, n_off, Yh, m_off, p)
+        e2e_s.append(time.perf_counter() - t0)
+    xfer = ctx.last_timing()
+    assert np.allclose(r["R"], got["R"]) and np.allclose(r["t"], got["t"])
+
+    # the plain per-pair form: the same pairs, one lsgcpd_register call each
+    def per_pair():
+        out = []
+        for i in range(P):
+            out.append(ctx.register(Xd[int(n_off[i]):int(n_off[i + 1])], Yd[int(m_off[i]):int(m_off[i + 1])], p))
+        return out
+    per_pair()
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    singles = per_pair()
+    e1.record(stream)
+    e1.synchronize()
+    pp_ms = e0.elapsed_time(e1)
+    pp_pairs = float(sum(s["iters"] * n for s, n in zip(singles, nm)))
+
+    ms = statistics.mean(step_ms)
+    e2e_ms = statistics.mean(e2e_s) * 1e3
+    if ws > 1:
+        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(tt[0]), float(tt[1])
+    value = ws * pairs_per_step / (ms / 1e3)
+    e2e_value = ws * pairs_per_step / (e2e_ms / 1e3)
+    t_launch = statistics.mean(estep_ms) / iters_run / 1e3
+    per_launch = float(nm.sum())
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * per_launch / t_launch / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "estep_kernel (whole batch per launch)",
+            "ms_per_launch": round(t_launch * 1e3, 5), "pairs_per_s_per_launch": per_launch / t_launch,
+            "counted": f"{FLOPS_PER_PAIR} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, sum N_i M_i pairs per launch",
+            "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch_256_pairs_500_20000", "pairs": P, "sum_N": int(Ns.sum()),
+                      "sum_M": int(Ms.sum()), "sum_NM": int(nm.sum()), "em_iters": iters, "knn_k": 10, "w": 0.1,
+                      "alpha_max": 2.0, "lambda": 0.2, "seed": seed, "e_step": "fp32 (packed f32x2) + ex2.approx",
+                      "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
+                      "parallelism": f"replicas x{ws} (independent batches per GPU)"},
+           "em_iters_per_s": ws * iters_run / (ms / 1e3),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
+                   "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4), "clock": "host wall"},
+           "roofline": roof, "clocks": clk, "gpu_launches": launches, "iters_run": iters_run,
+           "per_pair_form": {"value": pp_pairs / (pp_ms / 1e3), "unit": UNIT, "ms_per_step": round(pp_ms, 3),
+                             "calls": P, "batched_speedup": round((pp_ms / pp_pairs) / (ms / pairs_per_step), 3)}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        q = pairs[int(np.argmax(nm))]
+        pre = oracle.preprocess(q["Y"], 10, 2.0, 0.2)
+        V, _ = oracle.volume(q["Y"])
+        ns = min(len(q["X"]), 1000)
+        t0 = time.perf_counter()
+        oracle.estep(q["X"][:ns], q["Y"], pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), 0.05, 0.1, V)
+        rate = ns * len(q["Y"]) / (time.perf_counter() - t0)
+        ns = max(1, min(len(q["X"]), int(15.0 * rate / len(q["Y"]))))
+        t0 = time.perf_counter()
+        oracle.estep(q["X"][:ns], q["Y"], pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), 0.05, 0.1, V)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ns * len(q["Y"]) / dt, "unit": UNIT, "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "cpu": oracle.cpu_model(), "seconds": round(dt, 2),
+                               "sample": f"one E step over {ns} sources x {len(q['Y'])} targets of the largest pair"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     """The FP64 oracle as it stands on this host's cores: each step is one EM
     iteration (E step over a bounded subset of the sources, all targets), sized so
@@ -360,6 +518,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_ours(args)
 

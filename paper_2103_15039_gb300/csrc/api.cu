@@ -45,8 +45,8 @@ struct lsgcpd_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  DevBuf<float> X_in, Y_in, rec, part, knn_d, kap_n, gam_n;
-  DevBuf<float4> xs, y4;
+  DevBuf<float> X_in, Y_in, rec, part, knn_d, ls_n, gam_n;
+  DevBuf<float4> xs, y4, yl;
   DevBuf<int> knn_i, knn_idx, tab;
   DevBuf<long long> off64;
   DevBuf<double> rows, red, trace, io, mom;
@@ -203,9 +203,10 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
   };
   grow(c->xs, n_pad);
   grow(c->rec, m_pad * kPlanes);
+  grow(c->yl, m_pad);
   grow(c->part, estep_partial_floats(g));
   grow(c->rows, static_cast<size_t>(g.combine_ctas) * kGlob);
-  grow(c->kap_n, n_pad);
+  grow(c->ls_n, n_pad);
   grow(c->gam_n, n_pad);
   grow(c->tab, p.tab.size());
   grow(c->off64, p.off64.size());
@@ -344,7 +345,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   const int splits = knn_splits(g, c->num_sms);
   LSG_CUDA(launch_knn(plan, d, Yd, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, s), "knn");
   LSG_CUDA(launch_geometry(plan, d, Yd, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
-                           nullptr, nullptr, nullptr, s),
+                           c->yl.p, nullptr, nullptr, nullptr, s),
            "geometry");
   launches += 2 + 4 + 3 + 1;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
@@ -359,7 +360,8 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   }
   // one shift mode for the whole batch: fixed shift only if it is safe for every pair
   const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
-  int mode = 0;
+  // per-source shifts also when l_m varies (the uniform-shift moments assume one l)
+  int mode = p->include_alpha_norm ? 1 : 0;
   for (int i = 0; i < P; ++i) mode |= choose_mode(p->w, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
   if (iters > 0) {
     GraphKey key;
@@ -382,14 +384,13 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       cudaError_t ce = cudaSuccess;
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess && mode == 1) ce = launch_shift(plan, d, c->xs.p, c->rec.p, c->kap_n.p, c->gam_n.p, s);
-        if (ce == cudaSuccess)
-          ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode ? c->kap_n.p : nullptr, c->part.p, c->status, s);
+        if (ce == cudaSuccess) ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
+        if (ce == cudaSuccess && mode == 1) ce = launch_shift(plan, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s);
+        if (ce == cudaSuccess) ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
-          ce = launch_combine(plan, d, c->xs.p, c->part.p, mode ? c->kap_n.p : nullptr, mode ? c->gam_n.p : nullptr,
-                              c->rows.p, nullptr, s);
+          ce = launch_combine(plan, d, c->xs.p, c->part.p, mode, c->ls_n.p, c->gam_n.p, c->rows.p, nullptr, s);
         if (ce == cudaSuccess) ce = launch_final_reduce(plan, d, c->rows.p, c->mom.p, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
@@ -411,7 +412,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       c->gkey = key;
     }
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * (mode ? 5 : 4);
+    launches += static_cast<int64_t>(iters) * (mode ? 6 : 5);
   }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");
@@ -524,8 +525,8 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->kap_n.p, c->gam_n.p,
-                  c->xs.p,   c->y4.p,      c->knn_i.p, c->knn_idx.p, c->tab.p, c->off64.p, c->rows.p,
+  void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->ls_n.p, c->gam_n.p,
+                  c->xs.p,   c->y4.p,  c->yl.p,      c->knn_i.p, c->knn_idx.p, c->tab.p, c->off64.p, c->rows.p,
                   c->red.p,  c->trace.p,   c->io.p,  c->mom.p,   c->st.p,    c->status,  c->done_count};
   for (void* q : bufs)
     if (q) cudaFree(q);
@@ -581,8 +582,8 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   const int splits = knn_splits(plan.g, c->num_sms);
   int* idx = knn_idx ? knn_idx : c->knn_idx.p;
   LSG_CUDA(launch_knn(plan, d, Y, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, idx, s), "knn");
-  LSG_CUDA(launch_geometry(plan, d, Y, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p, normals,
-                           kappa, alpha, s),
+  LSG_CUDA(launch_geometry(plan, d, Y, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p, c->yl.p,
+                           normals, kappa, alpha, s),
            "geometry");
   c->launches = 7;
   int status = 0;
@@ -622,18 +623,18 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   const DevParams dp = dev_params(p);
   LSG_CUDA(launch_init(plan, d, X, Y, dp, false, c->red.p, c->xs.p, s), "center");
   LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
-  LSG_CUDA(launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c->rec.p, s), "pack");
-  const int mode = choose_mode(p->w, sigma2, volume, M, p->include_alpha_norm ? 12.0 : 0.0);
-  int64_t launches = 9;
+  LSG_CUDA(launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c->rec.p, c->yl.p, s), "pack");
+  const int mode = p->include_alpha_norm ? 1 : choose_mode(p->w, sigma2, volume, M, 0.0);
+  int64_t launches = 10;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
+  LSG_CUDA(launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s), "prescale");
   if (mode == 1) {
-    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, c->kap_n.p, c->gam_n.p, s), "shift");
+    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s), "shift");
     ++launches;
   }
-  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode ? c->kap_n.p : nullptr, c->part.p, c->status, s), "estep");
+  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode ? c->kap_n.p : nullptr, mode ? c->gam_n.p : nullptr,
-                          c->rows.p, per_n, s),
+  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, c->ls_n.p, c->gam_n.p, c->rows.p, per_n, s),
            "combine");
   LSG_CUDA(launch_final_reduce(plan, d, c->rows.p, c->mom.p, s), "reduce");
   launches += 3;

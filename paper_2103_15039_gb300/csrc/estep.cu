@@ -1,27 +1,33 @@
 // E step of LSG-CPD on sm_103a (Eq. (5) evaluated in the form of Eq. (9)).
 //
 // For every source n and every target m (Eq. (2)):
-//   r_mn = z_n - y_m,  d_mn = |r|^2 + alpha_m (n_m . r)^2 = r . u,  u = Lambda_m r = r + (a_m . r) a_m,
-//   a = sqrt(alpha) n,  P_mn = pi_m e^{-d/(2 s2)} / (sum_k pi_k e^{-d_k/(2 s2)} + gamma_n),
+//   r_mn = z_n - y_m,  d_mn = |r|^2 + alpha_m (n_m . r)^2 = |r|^2 + (a_m . r)^2,  a = sqrt(alpha) n,
+//   P_mn = pi_m e^{-d/(2 s2)} / (sum_k pi_k e^{-d_k/(2 s2)} + gamma_n),
 //   gamma_n = w/(1-w) (2 pi s2)^{3/2} / V.
-// The kernel never forms P.  It evaluates e_mn = 2^(l_m - c d_mn - L_n) with
-// c = log2(e)/(2 s2) and a per-source shift L_n, and accumulates 11 per-source
-// moments from which the M step's sufficient statistics follow by one division
-// (combine kernel below):
-//   S0 = sum e, h = sum e u (= rho + beta of the residual form), W = sum e a a^T,
-//   D' = sum e (d + kappa_n),  kappa_n = L_n / c.
-// Folding kappa_n into the squared distance makes the shift free in the hot
-// loop; the combine subtracts kappa_n S0.
+// The kernel never forms P.  With c = log2(e)/(2 s2) and coordinates scaled by
+// sqrt(c) (z^ = sqrt(c) z, y^ = sqrt(c) y, so that c d = |z^ - y^|^2 + (a . (z^ - y^))^2)
+// it evaluates e_mn = 2^-q_mn with
+//   q_mn = c d_mn + lambda_m (+ L_n),   lambda_m = L - l_m  (or -l_m with per-source shifts),
+// l_m = log2 pi_m and L (L_n) the log2 shift, and accumulates per source
+//   S0 = sum e,  B = sum e b_m (b_m = Lambda_m y_m),  W = sum e a a^T,  Dq = sum e q
+// (+ El = sum e lambda_m with per-source shifts).  The combine turns them into
+// the M step's statistics with one division per source:
+//   sum_m e Lambda_m r_mn = S0 z + W z - B  (Lambda_m = I + a a^T),
+//   sum_m e d_mn = (Dq - lambda S0) / c     (lambda uniform; else Dq - L_n S0 - El).
+// Per pair that is 21 packed-FP32 operations for two targets at once (3 adds,
+// 3 for a . r, 4 for q, 11 accumulations) and two MUFU.EX2.
 //
 // Hot-loop layout (GB300):
-//  * a CTA = 8 warps (S = 4) or 4 warps; each thread owns S sources (z_n duplicated into both
-//    halves of an FP32x2 register) and 11 FP32x2 accumulators per source;
+//  * a CTA = 8 warps (S = 4) or 4 warps; each thread owns S sources (z^_n duplicated into both
+//    halves of an FP32x2 register) and 11 (12) FP32x2 accumulators per source;
 //  * the two halves of every packed register belong to two consecutive
 //    targets, so every operation of the pair update is one packed
-//    FADD2/FMUL2/FFMA2 (24 per target pair per source) plus two MUFU.EX2;
-//  * target tiles (kTile records, 6.5 KB) stream into a 4-stage shared-memory
+//    FADD2/FMUL2/FFMA2;
+//  * target tiles (kTile records, 8 KB) stream into a 4-stage shared-memory
 //    ring by cp.async.bulk (TMA bulk copy) completing on mbarriers; every warp
-//    reads the tile with broadcast 128-bit shared loads;
+//    reads the tile with broadcast shared loads;
+//  * the sigma-dependent record planes are rewritten once per EM iteration by a
+//    small O(M) pass (prescale), so the hot loop needs no per-target setup;
 //  * work = (source block) x (target tile) units split stream-K style over a
 //    grid of (SM count x resident CTAs); a CTA flushes its FP32 partial
 //    moments at block boundaries and every seg_cap tiles, so FP32 sums stay
@@ -43,12 +49,6 @@ __host__ __device__ constexpr int warps_for() { return S >= 4 ? 8 : 4; }
 template <int S>
 __host__ __device__ constexpr int min_ctas_for() { return S >= 4 ? 1 : 3; }
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -90,92 +90,95 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+__device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
+  return y;
+}
+
 struct Src {
-  float2 z0, z1, z2;  // z_n in both halves
-  float2 kp;          // kappa_n in both halves
+  float2 z0, z1, z2;  // z^_n in both halves
+  float2 ls;          // L_n in both halves (per-source shift mode)
 };
 
 struct Acc {
-  float2 s0, h0, h1, h2, w00, w01, w02, w11, w12, w22, d;
+  float2 s0, b0, b1, b2, w00, w01, w02, w11, w12, w22, d, el;
 };
 
 struct Tgt {  // two consecutive targets, one per half
-  float2 ny0, ny1, ny2, a0, a1, a2, q00, q01, q02, q11, q12, q22, l;
+  float2 ny0, ny1, ny2, lam, a0, a1, a2, q00, q01, q02, q11, q12, q22, b0, b1, b2;
 };
 
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
-// One source against two targets: 24 packed FP32 operations and 2 EX2.
-__device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g, float2 nc) {
+// One source against two targets: 21 packed FP32 operations (22 + 1 with
+// per-source shifts) and 2 EX2.
+template <bool MAXS>
+__device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g) {
   const float2 r0 = __fadd2_rn(s.z0, g.ny0);
   const float2 r1 = __fadd2_rn(s.z1, g.ny1);
   const float2 r2 = __fadd2_rn(s.z2, g.ny2);
-  float2 v = __fmul2_rn(g.a0, r0);  // v = a . r
+  float2 v = __fmul2_rn(g.a0, r0);  // v = a . r^
   v = __ffma2_rn(g.a1, r1, v);
   v = __ffma2_rn(g.a2, r2, v);
-  const float2 u0 = __ffma2_rn(v, g.a0, r0);  // u = r + v a = Lambda r
-  const float2 u1 = __ffma2_rn(v, g.a1, r1);
-  const float2 u2 = __ffma2_rn(v, g.a2, r2);
-  float2 dd = __ffma2_rn(r2, u2, s.kp);  // d + kappa_n = r . u + kappa_n
-  dd = __ffma2_rn(r1, u1, dd);
-  dd = __ffma2_rn(r0, u0, dd);
-  const float2 x = __ffma2_rn(dd, nc, g.l);  // l_m - c (d + kappa_n)
+  float2 q = MAXS ? __fadd2_rn(g.lam, s.ls) : g.lam;  // q = c d + lambda_m (+ L_n)
+  q = __ffma2_rn(r0, r0, q);
+  q = __ffma2_rn(r1, r1, q);
+  q = __ffma2_rn(r2, r2, q);
+  q = __ffma2_rn(v, v, q);
   float2 e;
-  e.x = ex2_approx(x.x);
-  e.y = ex2_approx(x.y);
+  e.x = ex2_neg(q.x);
+  e.y = ex2_neg(q.y);
   A.s0 = __fadd2_rn(A.s0, e);
-  A.h0 = __ffma2_rn(e, u0, A.h0);
-  A.h1 = __ffma2_rn(e, u1, A.h1);
-  A.h2 = __ffma2_rn(e, u2, A.h2);
+  A.b0 = __ffma2_rn(e, g.b0, A.b0);
+  A.b1 = __ffma2_rn(e, g.b1, A.b1);
+  A.b2 = __ffma2_rn(e, g.b2, A.b2);
   A.w00 = __ffma2_rn(e, g.q00, A.w00);
   A.w01 = __ffma2_rn(e, g.q01, A.w01);
   A.w02 = __ffma2_rn(e, g.q02, A.w02);
   A.w11 = __ffma2_rn(e, g.q11, A.w11);
   A.w12 = __ffma2_rn(e, g.q12, A.w12);
   A.w22 = __ffma2_rn(e, g.q22, A.w22);
-  A.d = __ffma2_rn(e, dd, A.d);
+  A.d = __ffma2_rn(e, q, A.d);
+  if (MAXS) A.el = __ffma2_rn(e, g.lam, A.el);
 }
 
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-
-template <int S>
-__device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)[S], Acc (&acc)[S],
-                                             float2 nc) {
-  const float4* T4 = reinterpret_cast<const float4*>(tile);
-  constexpr int Q = kTile / 4;
-#pragma unroll 1
-  for (int q = 0; q < Q; ++q) {
-    float4 P[kPlanes];
+// All pairs of one tile: every thread walks the tile two targets at a time
+// (broadcast 64-bit shared loads of the 16 planes).
+template <int S, bool MAXS>
+__device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)[S], Acc (&acc)[S]) {
+  const float2* T2 = reinterpret_cast<const float2*>(tile);
+  constexpr int H = kTile / 2;
+#pragma unroll 2
+  for (int q = 0; q < H; ++q) {
+    Tgt g;
+    g.ny0 = T2[0 * H + q];
+    g.ny1 = T2[1 * H + q];
+    g.ny2 = T2[2 * H + q];
+    g.lam = T2[3 * H + q];
+    g.a0 = T2[4 * H + q];
+    g.a1 = T2[5 * H + q];
+    g.a2 = T2[6 * H + q];
+    g.q00 = T2[7 * H + q];
+    g.q01 = T2[8 * H + q];
+    g.q02 = T2[9 * H + q];
+    g.q11 = T2[10 * H + q];
+    g.q12 = T2[11 * H + q];
+    g.q22 = T2[12 * H + q];
+    g.b0 = T2[13 * H + q];
+    g.b1 = T2[14 * H + q];
+    g.b2 = T2[15 * H + q];
 #pragma unroll
-    for (int p = 0; p < kPlanes; ++p) P[p] = T4[p * Q + q];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      Tgt g;
-      g.ny0 = h ? hi2(P[0]) : lo2(P[0]);
-      g.ny1 = h ? hi2(P[1]) : lo2(P[1]);
-      g.ny2 = h ? hi2(P[2]) : lo2(P[2]);
-      g.a0 = h ? hi2(P[3]) : lo2(P[3]);
-      g.a1 = h ? hi2(P[4]) : lo2(P[4]);
-      g.a2 = h ? hi2(P[5]) : lo2(P[5]);
-      g.q00 = h ? hi2(P[6]) : lo2(P[6]);
-      g.q01 = h ? hi2(P[7]) : lo2(P[7]);
-      g.q02 = h ? hi2(P[8]) : lo2(P[8]);
-      g.q11 = h ? hi2(P[9]) : lo2(P[9]);
-      g.q12 = h ? hi2(P[10]) : lo2(P[10]);
-      g.q22 = h ? hi2(P[11]) : lo2(P[11]);
-      g.l = h ? hi2(P[12]) : lo2(P[12]);
-#pragma unroll
-      for (int s = 0; s < S; ++s) pair_update(acc[s], src[s], g, nc);
-    }
+    for (int s = 0; s < S; ++s) pair_update<MAXS>(acc[s], src[s], g);
   }
 }
 
+template <bool MAXS>
 __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc& a) {
   dst[0 * SB + nl] = a.s0.x + a.s0.y;
-  dst[1 * SB + nl] = a.h0.x + a.h0.y;
-  dst[2 * SB + nl] = a.h1.x + a.h1.y;
-  dst[3 * SB + nl] = a.h2.x + a.h2.y;
+  dst[1 * SB + nl] = a.b0.x + a.b0.y;
+  dst[2 * SB + nl] = a.b1.x + a.b1.y;
+  dst[3 * SB + nl] = a.b2.x + a.b2.y;
   dst[4 * SB + nl] = a.w00.x + a.w00.y;
   dst[5 * SB + nl] = a.w01.x + a.w01.y;
   dst[6 * SB + nl] = a.w02.x + a.w02.y;
@@ -183,6 +186,7 @@ __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc&
   dst[8 * SB + nl] = a.w12.x + a.w12.y;
   dst[9 * SB + nl] = a.w22.x + a.w22.y;
   dst[10 * SB + nl] = a.d.x + a.d.y;
+  if (MAXS) dst[11 * SB + nl] = a.el.x + a.el.y;
 }
 
 // Producer/consumer cursor over a CTA's units: (source block, unit) advancing
@@ -195,10 +199,10 @@ struct Cursor {
   }
 };
 
-template <int S>
+template <int S, bool MAXS>
 __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
-                 const float* __restrict__ kap_n, float* __restrict__ part, const int* __restrict__ tab,
+                 const float* __restrict__ ls_n, float* __restrict__ part, const int* __restrict__ tab,
                  const int* __restrict__ done_count, int* __restrict__ status, Geo g) {
   constexpr int SB = warps_for<S>() * 32 * S;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -248,13 +252,12 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     if (seg_end > block_end) seg_end = block_end;
     if (seg_end > u1) seg_end = u1;
 
-    const float2 nc = dup(sp->neg_c);
+    const float sqc = sp->sqc;
     float Rm[9], tv[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Rm[q] = sp->Rf[q];
 #pragma unroll
     for (int q = 0; q < 3; ++q) tv[q] = sp->tf[q];
-    const float kap_uniform = sp->kap;
     Src src[S];
     Acc acc[S];
 #pragma unroll
@@ -266,12 +269,12 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
       const float z0 = fmaf(Rm[0], x.x, fmaf(Rm[1], x.y, fmaf(Rm[2], x.z, tv[0])));
       const float z1 = fmaf(Rm[3], x.x, fmaf(Rm[4], x.y, fmaf(Rm[5], x.z, tv[1])));
       const float z2 = fmaf(Rm[6], x.x, fmaf(Rm[7], x.y, fmaf(Rm[8], x.z, tv[2])));
-      src[s2].z0 = dup(z0);
-      src[s2].z1 = dup(z1);
-      src[s2].z2 = dup(z2);
-      src[s2].kp = dup(kap_n ? kap_n[n] : kap_uniform);
+      src[s2].z0 = dup(sqc * z0);
+      src[s2].z1 = dup(sqc * z1);
+      src[s2].z2 = dup(sqc * z2);
+      src[s2].ls = dup(MAXS ? ls_n[n] : 0.f);
       const float2 zero = make_float2(0.f, 0.f);
-      acc[s2] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
+      acc[s2] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
     }
 
     for (; u < seg_end; ++u, ++i) {
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
       const uint32_t parity = static_cast<uint32_t>(i / kStages) & 1u;
       const bool ok = mbar_wait(&full[stage], parity);
       if (!ok && lane == 0) atomicOr(status, kStatusTimeout);
-      tile_compute<S>(tiles + stage * kTileFloats, src, acc, nc);
+      tile_compute<S, MAXS>(tiles + stage * kTileFloats, src, acc);
       if (__syncthreads_or(!ok)) {
         abort = true;
         break;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     if (abort) break;
     float* dst = part + static_cast<size_t>(first_slot + seg) * kMom * SB;
 #pragma unroll
-    for (int s2 = 0; s2 < S; ++s2) store_acc(dst, SB, warp * 32 * S + s2 * 32 + lane, acc[s2]);
+    for (int s2 = 0; s2 < S; ++s2) store_acc<MAXS>(dst, SB, warp * 32 * S + s2 * 32 + lane, acc[s2]);
     ++seg;
   }
   if (abort && tid == 0) {
@@ -304,57 +307,75 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
 }
 
 // ---------------------------------------------------------------------------
-// Per-source shift for the max-shift mode (used when w = 0 or the fixed shift
-// could overflow FP32): L_n = max(log2 gamma, max_m (l_m - c d_mn)) over the
-// targets of the source's pair.
+// Prescale: the sigma-dependent planes of every record slot for the current
+// state of its pair: -sqrt(c) y (3) and lambda_m (L - l_m, or -l_m with
+// per-source shifts; kPadLambda for padding).  One thread per slot.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTile)
+    prescale_kernel(const float4* __restrict__ yl, const EmState* __restrict__ st, const int* __restrict__ tab,
+                    const int* __restrict__ done_count, int mode, float* __restrict__ rec, Geo g) {
+  if (*done_count >= g.P) return;
+  const int tile = blockIdx.x;
+  const EmState* sp = st + tab[g.o_tile_pair + tile];
+  if (sp->done) return;
+  const long long slot = static_cast<long long>(tile) * kTile + threadIdx.x;
+  const float4 y = yl[slot];
+  const bool pad = y.w == -INFINITY;
+  const float sqc = sp->sqc;
+  float* r = rec + static_cast<size_t>(tile) * kTileFloats + threadIdx.x;
+  r[0 * kTile] = pad ? 0.f : -sqc * y.x;
+  r[1 * kTile] = pad ? 0.f : -sqc * y.y;
+  r[2 * kTile] = pad ? 0.f : -sqc * y.z;
+  r[3 * kTile] = pad ? kPadLambda : (mode ? -y.w : sp->L - y.w);
+}
+
+// ---------------------------------------------------------------------------
+// Per-source shift for the max-shift mode (used when w = 0, when a fixed shift
+// could overflow FP32, or when l_m varies): L_n = max(log2 gamma, max_m (l_m - c d_mn))
+// over the targets of the source's pair.  Planes 0-6 after prescale with
+// lambda_m = -l_m give l_m - c d = -(lambda_m + |r^|^2 + (a . r^)^2).
 // ---------------------------------------------------------------------------
 constexpr int kShiftThreads = 128;
 
 __global__ void __launch_bounds__(kShiftThreads)
     shift_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
                  const int* __restrict__ tab, const long long* __restrict__ off64,
-                 const int* __restrict__ done_count, float* __restrict__ kap_n, float* __restrict__ gam_n, Geo g) {
+                 const int* __restrict__ done_count, float* __restrict__ ls_n, float* __restrict__ gam_n, Geo g) {
   __shared__ __align__(16) float tile[7 * kTile];
   if (*done_count >= g.P) return;
   // every CTA covers kShiftThreads sources of one source block (SB is a multiple)
   const long long n = static_cast<long long>(blockIdx.x) * kShiftThreads + threadIdx.x;
   const int b = static_cast<int>(n / g.SB);
   const int pair = tab[g.o_block_pair + b];
-  const long long local = n - static_cast<long long>(tab[g.o_blk_off + pair]) * g.SB;
-  const long long Np = off64[pair + 1] - off64[pair];
-  const bool valid = local < Np;
   const EmState* sp = st + pair;
+  if (sp->done) return;  // uniform over the CTA
   const float4 x = xs[n];
   const float* R = sp->Rf;
-  const float z0 = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, sp->tf[0])));
-  const float z1 = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, sp->tf[1])));
-  const float z2 = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, sp->tf[2])));
-  const float nc = sp->neg_c;
-  float best = -INFINITY;
+  const float sqc = sp->sqc;
+  const float z0 = sqc * fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, sp->tf[0])));
+  const float z1 = sqc * fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, sp->tf[1])));
+  const float z2 = sqc * fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, sp->tf[2])));
+  float best = INFINITY;  // min_m q_m
   const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
   for (int t = t0; t < t1; ++t) {
     __syncthreads();
-    for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) {
-      const int pl = e / kTile, j = e % kTile;
-      tile[e] = rec[static_cast<size_t>(t) * kTileFloats + (pl < 6 ? pl : 12) * kTile + j];
-    }
+    for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) tile[e] = rec[static_cast<size_t>(t) * kTileFloats + e];
     __syncthreads();
 #pragma unroll 4
     for (int j = 0; j < kTile; ++j) {
       const float r0 = z0 + tile[0 * kTile + j];
       const float r1 = z1 + tile[1 * kTile + j];
       const float r2 = z2 + tile[2 * kTile + j];
-      const float v = fmaf(tile[3 * kTile + j], r0, fmaf(tile[4 * kTile + j], r1, tile[5 * kTile + j] * r2));
-      const float d = fmaf(v, v, fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
-      best = fmaxf(best, fmaf(d, nc, tile[6 * kTile + j]));
+      const float v = fmaf(tile[4 * kTile + j], r0, fmaf(tile[5 * kTile + j], r1, tile[6 * kTile + j] * r2));
+      const float q = fmaf(v, v, fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, tile[3 * kTile + j]))));
+      best = fminf(best, q);
     }
   }
-  if (!valid) return;
+  // padding sources (zero x) get finite values too; they are never read back
   const float Lg = sp->L;  // log2 gamma (-inf without outlier term)
-  const float L = fmaxf(best, Lg);
-  // kappa = L / c with c = -neg_c; gamma' = 2^(log2 gamma - L)
-  kap_n[n] = -L / nc;
-  gam_n[n] = exp2f(Lg - L);
+  const float L = fmaxf(-best, Lg);
+  ls_n[n] = L;
+  gam_n[n] = exp2f(Lg - L);  // gamma'_n = 2^(log2 gamma - L_n)
 }
 
 // ---------------------------------------------------------------------------
@@ -375,7 +396,7 @@ constexpr int kCPad = kGlob + 1;  // odd row pitch: conflict-free transposition
 __global__ void __launch_bounds__(kCombineThreads)
     combine_kernel(const float4* __restrict__ xs, const float* __restrict__ part, const int* __restrict__ tab,
                    const long long* __restrict__ off64, const EmState* __restrict__ st,
-                   const int* __restrict__ done_count, const float* __restrict__ kap_n,
+                   const int* __restrict__ done_count, int mode, const float* __restrict__ ls_n,
                    const float* __restrict__ gam_n, double* __restrict__ rows, float* __restrict__ per_n, Geo g) {
   __shared__ float buf[kCombineWarps][32 * kCPad];
   __shared__ double acc[kCombineWarps][kGlob];
@@ -392,10 +413,11 @@ __global__ void __launch_bounds__(kCombineThreads)
   const long long Np = off64[pair + 1] - off64[pair];
   const bool valid = local < Np;
   const int nl = static_cast<int>(n - static_cast<long long>(b) * g.SB);
+  const int nmom = mode ? kMom : kMom - 1;
   float m[kMom], cmp[kMom];
 #pragma unroll
   for (int k = 0; k < kMom; ++k) m[k] = cmp[k] = 0.f;
-  float x0 = 0.f, x1 = 0.f, x2 = 0.f, kap = 0.f, gp = 0.f, L = 0.f;
+  float x0 = 0.f, x1 = 0.f, x2 = 0.f, gp = 0.f, L = 0.f, lam = 0.f;
   if (valid) {
     const int first = tab[g.o_block_slot + 2 * b];
     const int count = tab[g.o_block_slot + 2 * b + 1];
@@ -403,32 +425,43 @@ __global__ void __launch_bounds__(kCombineThreads)
       const float* src = part + static_cast<size_t>(j) * kMom * g.SB + nl;
 #pragma unroll
       for (int k = 0; k < kMom; ++k) {  // Kahan summation of the pieces
-        const float y = src[static_cast<size_t>(k) * g.SB] - cmp[k];
-        const float t = m[k] + y;
-        cmp[k] = (t - m[k]) - y;
-        m[k] = t;
+        if (k < nmom) {
+          const float y = src[static_cast<size_t>(k) * g.SB] - cmp[k];
+          const float t = m[k] + y;
+          cmp[k] = (t - m[k]) - y;
+          m[k] = t;
+        }
       }
     }
     const float4 x = xs[n];
     x0 = x.x;
     x1 = x.y;
     x2 = x.z;
-    if (kap_n) {
-      kap = kap_n[n];
+    if (mode) {
+      L = ls_n[n];
       gp = gam_n[n];
-      L = -kap * sp->neg_c;
+      lam = L;  // sum e c d = Dq - L_n S0 - El
     } else {
-      kap = sp->kap;
-      gp = (sp->log2_wodds > -INFINITY) ? 1.f : 0.f;
       L = sp->L;
+      gp = (sp->log2_wodds > -INFINITY) ? 1.f : 0.f;
+      lam = sp->lam;  // sum e c d = Dq - lambda S0
     }
   }
   const float S0 = m[0];
-  const float D = m[10] - kap * S0;
+  // z = R x + t (centred frame), h = S0 z + W z - B = sum e Lambda_m r_mn
+  const float* Rr = sp->Rf;
+  const float z0 = fmaf(Rr[0], x0, fmaf(Rr[1], x1, fmaf(Rr[2], x2, sp->tf[0])));
+  const float z1 = fmaf(Rr[3], x0, fmaf(Rr[4], x1, fmaf(Rr[5], x2, sp->tf[1])));
+  const float z2 = fmaf(Rr[6], x0, fmaf(Rr[7], x1, fmaf(Rr[8], x2, sp->tf[2])));
+  const float hr0 = fmaf(S0 + m[4], z0, fmaf(m[5], z1, fmaf(m[6], z2, -m[1])));
+  const float hr1 = fmaf(m[5], z0, fmaf(S0 + m[7], z1, fmaf(m[8], z2, -m[2])));
+  const float hr2 = fmaf(m[6], z0, fmaf(m[8], z1, fmaf(S0 + m[9], z2, -m[3])));
+  const float cD = fmaf(-lam, S0, m[10]) - (mode ? m[11] : 0.f);  // sum e c d
+  const float D = cD / -sp->neg_c;
   const float denom = S0 + gp;
   const float inv = denom > 0.f ? 1.f / denom : 0.f;
   const float Pb = S0 * inv;
-  const float h[3] = {m[1] * inv, m[2] * inv, m[3] * inv};
+  const float h[3] = {hr0 * inv, hr1 * inv, hr2 * inv};
   const float W00 = m[4] * inv, W01 = m[5] * inv, W02 = m[6] * inv, W11 = m[7] * inv, W12 = m[8] * inv,
               W22 = m[9] * inv;
   const float Dn = D * inv;
@@ -510,11 +543,11 @@ __global__ void final_reduce_kernel(const double* __restrict__ rows, const int* 
   if (lane == 0) mom[static_cast<size_t>(pair) * kGlob + j] = v;
 }
 
-template <int S>
+template <int S, bool MAXS>
 cudaError_t launch_estep_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
-                           const float* kap_n, float* part, int* status, cudaStream_t s) {
-  estep_kernel<S><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, kap_n, part, d.tab,
-                                                                     d.done_count, status, p.g);
+                           const float* ls_n, float* part, int* status, cudaStream_t s) {
+  estep_kernel<S, MAXS><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, ls_n, part, d.tab,
+                                                                           d.done_count, status, p.g);
   return cudaGetLastError();
 }
 
@@ -523,11 +556,11 @@ int resident_ctas(int S) {
   const size_t smem = kStages * kTileBytes + kStages * sizeof(uint64_t);
   cudaError_t e = cudaSuccess;
   if (S == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4>, warps_for<4>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4, false>, warps_for<4>() * 32, smem);
   else if (S == 2)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2>, warps_for<2>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2, false>, warps_for<2>() * 32, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1>, warps_for<1>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1, false>, warps_for<1>() * 32, smem);
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -652,6 +685,10 @@ BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long lon
     bs[2 * q + 1] = count[q];
   }
   g.o_block_slot = put(bs);
+  std::vector<int> tile_pair(g.T);
+  for (int i = 0; i < P; ++i)
+    for (int t = tile_off[i]; t < tile_off[i + 1]; ++t) tile_pair[t] = i;
+  g.o_tile_pair = put(tile_pair);
   p.off64.assign(2 * static_cast<size_t>(P) + 2, 0);
   for (int i = 0; i < P; ++i) {
     p.off64[i + 1] = p.off64[i] + N[i];
@@ -662,27 +699,40 @@ BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long lon
 
 size_t estep_partial_floats(const Geo& g) { return static_cast<size_t>(g.total_slots) * kMom * g.SB; }
 
-cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
-                         const float* kap_n, float* part, int* status, cudaStream_t s) {
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode,
+                         const float* ls_n, float* part, int* status, cudaStream_t s) {
+  if (mode) {
+    switch (p.g.S) {
+      case 4: return launch_estep_t<4, true>(p, d, xs, rec, ls_n, part, status, s);
+      case 2: return launch_estep_t<2, true>(p, d, xs, rec, ls_n, part, status, s);
+      default: return launch_estep_t<1, true>(p, d, xs, rec, ls_n, part, status, s);
+    }
+  }
   switch (p.g.S) {
-    case 4: return launch_estep_t<4>(p, d, xs, rec, kap_n, part, status, s);
-    case 2: return launch_estep_t<2>(p, d, xs, rec, kap_n, part, status, s);
-    default: return launch_estep_t<1>(p, d, xs, rec, kap_n, part, status, s);
+    case 4: return launch_estep_t<4, false>(p, d, xs, rec, nullptr, part, status, s);
+    case 2: return launch_estep_t<2, false>(p, d, xs, rec, nullptr, part, status, s);
+    default: return launch_estep_t<1, false>(p, d, xs, rec, nullptr, part, status, s);
   }
 }
 
-cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* kap_n,
-                         float* gam_n, cudaStream_t s) {
-  const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
-  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.off64,
-                                                                      d.done_count, kap_n, gam_n, p.g);
+cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, int mode, float* rec,
+                            cudaStream_t s) {
+  prescale_kernel<<<p.g.T, kTile, 0, s>>>(yl, d.st, d.tab, d.done_count, mode, rec, p.g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part,
-                           const float* kap_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s) {
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* ls_n,
+                         float* gam_n, cudaStream_t s) {
+  const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
+  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.off64,
+                                                                      d.done_count, ls_n, gam_n, p.g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
+                           const float* ls_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s) {
   combine_kernel<<<p.g.combine_ctas, kCombineThreads, 0, s>>>(xs, part, d.tab, d.off64, d.st, d.done_count,
-                                                              kap_n, gam_n, rows, per_n, p.g);
+                                                              mode, ls_n, gam_n, rows, per_n, p.g);
   return cudaGetLastError();
 }
 

@@ -18,19 +18,30 @@ namespace lsg {
 // tile-major and plane-minor so that a tile of kTile targets is one contiguous
 // block that a single bulk copy moves into shared memory:
 //   rec[tile][plane][kTile]
-// planes: -y (3), a = sqrt(alpha) n (3), a a^T (00,01,02,11,12,22), l
-// with l = log2 pi_m (+ 1/2 log2(1 + alpha_m) with the Gaussian constant).
-// A padding target has l = -inf, so it contributes exactly 0.
+// planes 0-3 are rewritten before every E step for the current sigma^2 (the
+// E step works in coordinates scaled by sqrt(c), c = log2(e) / (2 sigma^2), so
+// that c d_mn is a plain sum of squares):
+//   0-2  -sqrt(c) y
+//   3    lambda_m: L - l_m with the uniform shift L, or -l_m with per-source shifts
+//   4-6  a = sqrt(alpha) n
+//   7-12 a a^T (00,01,02,11,12,22)
+//   13-15 b = Lambda_m y = y + (a . y) a
+// with l_m = log2 pi_m (+ 1/2 log2(1 + alpha_m) with the Gaussian constant).
+// A padding target has lambda = kPadLambda, so it contributes exactly 0.
+// The unscaled centred y and l_m of every record slot are kept in yl[slot]
+// (float4; l = -inf marks padding).
 // ---------------------------------------------------------------------------
-constexpr int kPlanes = 13;
+constexpr int kPlanes = 16;
 constexpr int kTile = 128;
 constexpr int kTileFloats = kPlanes * kTile;
 constexpr int kTileBytes = kTileFloats * 4;
+constexpr float kPadLambda = 1e30f;
 
-// Per-source raw E-step moments accumulated by the hot kernel:
-//   S0 = sum e, h (3) = sum e Lambda_m r (Lambda_m = I + a a^T), W (6) = sum e a a^T,
-//   D' = sum e (d + kappa_n)
-constexpr int kMom = 11;
+// Per-source raw E-step moments accumulated by the hot kernel (e = 2^-q,
+// q = c d + lambda_m [+ L_n]):
+//   S0 = sum e, B (3) = sum e b_m, W (6) = sum e a a^T, Dq = sum e q,
+//   El = sum e lambda_m (per-source shift mode only)
+constexpr int kMom = 12;
 
 // Global moments per pair (see lsgcpd.h): N_P, sum D, H1 (12), G (60), sum Pout, NLL.
 constexpr int kGlob = 76;
@@ -58,6 +69,7 @@ struct EmState {
   double nll_const;     // per-source constant of -log p: -ln((1-w) (2 pi s2)^(-3/2)) at the E step
   double log2_V;        // log2 V
   double ln_1mw;        // ln(1 - w)
+  double log2_pi;       // log2 pi_m of the uniform prior, -log2 M
   int32_t done;         // EM finished (floor, tol or numeric failure)
   int32_t iter;         // iterations completed
   int32_t numeric_fail;
@@ -65,24 +77,29 @@ struct EmState {
   // E-step constants for the current (R, t, sigma2):
   float Rf[9];
   float tf[3];
-  float neg_c;          // -log2(e) / (2 sigma2)
-  float kap;            // uniform shift in distance units, L / c  (fixed-shift mode)
-  float L;              // uniform log2 shift (fixed-shift mode): log2 gamma
-  float pad1;
+  float neg_c;          // -c = -log2(e) / (2 sigma2)
+  float L;              // log2 gamma: the uniform log2 shift (-inf without outlier term)
+  float sqc;            // sqrt(c): the E step's coordinate scale
+  float lam;            // L - log2 pi: lambda_m of every target in the uniform-shift mode
 };
 
-// E-step constants for the current (R, t, sigma2) of the state.  The shift L
-// and the logarithms feed FP32 arithmetic only, so they are evaluated in FP32.
-__device__ inline void set_estep_constants(EmState* st) {
-  const float s2 = static_cast<float>(st->sigma2);
+// E-step constants for the current sigma2 (FP32: they feed FP32 arithmetic only).
+__device__ inline void set_sigma_constants(EmState* st, float s2) {
   const float lg = log2f(6.2831853f * s2);
   const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
+  const float c = 1.44269504f / (2.f * s2);  // log2(e) / (2 s2)
+  st->neg_c = -c;
+  st->L = L;
+  st->sqc = sqrtf(c);
+  st->lam = L - static_cast<float>(st->log2_pi);
+  st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
+}
+
+// E-step constants for the current (R, t, sigma2) of the state.
+__device__ inline void set_estep_constants(EmState* st) {
   for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
   for (int i = 0; i < 3; ++i) st->tf[i] = static_cast<float>(st->t[i]);
-  st->neg_c = -1.44269504f / (2.f * s2);  // -log2(e) / (2 s2)
-  st->L = L;
-  st->kap = L * (2.f * s2) * 0.69314718f;  // L / c
-  st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
+  set_sigma_constants(st, static_cast<float>(st->sigma2));
 }
 
 // Scalar parameters the device needs (a subset of lsgcpd_params).
@@ -118,6 +135,7 @@ struct DevParams {
 //   cta_slot[G+1]   first partial slot of each CTA
 //   cta_block[G]    source block of each CTA's first unit
 //   block_slot[2B]  (first slot, slot count) of each source block
+//   tile_pair[T]    pair of each target tile
 // Device int64 table: n_off[P+1], m_off[P+1] (offsets of the raw inputs).
 // ---------------------------------------------------------------------------
 struct Geo {
@@ -133,7 +151,7 @@ struct Geo {
   long long U;         // units
   long long max_n;     // largest N_i
   long long max_m;     // largest M_i
-  int o_blk_off, o_tile_off, o_block_pair, o_unit_off, o_cta_slot, o_cta_block, o_block_slot;
+  int o_blk_off, o_tile_off, o_block_pair, o_unit_off, o_cta_slot, o_cta_block, o_block_slot, o_tile_pair;
   int total_slots;
   int combine_ctas;    // B * SB / kCombineSources
 };
@@ -160,13 +178,17 @@ struct Dev {
 };
 
 // ----- E step (estep.cu) --------------------------------------------------------
-cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
-                         const float* kap_n, float* part, int* status, cudaStream_t s);
-cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* kap_n,
+// Shift modes: 0 = uniform shift L (fixed), 1 = per-source shift L_n (shift pass).
+// Rewrite the sigma-dependent record planes 0-3 from yl for the current state.
+cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, int mode, float* rec,
+                            cudaStream_t s);
+// mode 1 only: L_n and gamma'_n of every source.
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* ls_n,
                          float* gam_n, cudaStream_t s);
-cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part,
-                           const float* kap_n, const float* gam_n, double* rows, float* per_n,
-                           cudaStream_t s);
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode,
+                         const float* ls_n, float* part, int* status, cudaStream_t s);
+cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
+                           const float* ls_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s);
 // Sum each pair's combine rows (fixed order, FP64) into mom[P][kGlob]; one warp per moment.
 cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom,
                                 cudaStream_t s);
@@ -193,10 +215,11 @@ cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const 
 int knn_splits(const Geo& g, int num_sms);
 cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, int splits, float4* y4,
                        float* part_d, int* part_i, int* idx_out, cudaStream_t s);
+// Both write the static record planes 4-15 and yl.
 cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
-                            double alpha_max, double lambda, int alpha_norm, float* rec, float* normals,
-                            float* kappa, float* alpha, cudaStream_t s);
+                            double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
+                            float* normals, float* kappa, float* alpha, cudaStream_t s);
 cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals,
-                        const float* alpha, int alpha_norm, float* rec, cudaStream_t s);
+                        const float* alpha, int alpha_norm, float* rec, float4* yl, cudaStream_t s);
 
 }  // namespace lsg

@@ -540,13 +540,7 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     atomicAdd(done_count, 1);
   }
   // E-step constants (the rotation/translation copies were written above)
-  const float s2f = static_cast<float>(s2);
-  const float lg = log2f(6.2831853f * s2f);
-  const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
-  st->neg_c = -1.44269504f / (2.f * s2f);
-  st->L = L;
-  st->kap = L * (2.f * s2f) * 0.69314718f;
-  st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
+  set_sigma_constants(st, static_cast<float>(s2));
 }
 
 __global__ void __launch_bounds__(kMThreads) mstep_standalone_kernel(double* __restrict__ io, DevParams dp) {

@@ -55,8 +55,9 @@ struct Carve {
   double* rows;
   double* mom;
   float4* xs;
+  float4* yl;
   float* rec;
-  float* kap;
+  float* ls;
   float* gam;
   float* part;
 };
@@ -81,7 +82,8 @@ bool carve(unsigned char* base, const lsg::BatchPlan& p, Carve* c) {
   c->mom = reinterpret_cast<double*>(take(sizeof(double) * lsg::kGlob));
   c->xs = reinterpret_cast<float4*>(take(sizeof(float4) * n_pad));
   c->rec = reinterpret_cast<float*>(take(sizeof(float) * m_pad * lsg::kPlanes));
-  c->kap = reinterpret_cast<float*>(take(sizeof(float) * n_pad));
+  c->yl = reinterpret_cast<float4*>(take(sizeof(float4) * m_pad));
+  c->ls = reinterpret_cast<float*>(take(sizeof(float) * n_pad));
   c->gam = reinterpret_cast<float*>(take(sizeof(float) * n_pad));
   c->part = reinterpret_cast<float*>(take(sizeof(float) * lsg::estep_partial_floats(g)));
   return off <= kArenaBytes;
@@ -159,18 +161,18 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
   dp.volume = volume;
   if (e == cudaSuccess) e = lsg::launch_init(plan, d, X, Y, dp, false, c.red, c.xs, s);
   if (e == cudaSuccess) e = lsg::launch_estep_constants(c.st, sigma2, p->w, volume, R, t, s);
-  if (e == cudaSuccess) e = lsg::launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c.rec, s);
-  // fixed shift unless the outlier term is absent or a term could overflow FP32
+  if (e == cudaSuccess) e = lsg::launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c.rec, c.yl, s);
+  // fixed shift unless the outlier term is absent, a term could overflow FP32 or l_m varies
   int mode = 1;
-  if (p->w > 0.0) {
+  if (p->w > 0.0 && !p->include_alpha_norm) {
     const double L = log2(p->w) - log2(1.0 - p->w) + 1.5 * log2(2.0 * M_PI * sigma2) - log2(volume);
-    const double l_max = -log2(static_cast<double>(M)) + (p->include_alpha_norm ? 12.0 : 0.0);
+    const double l_max = -log2(static_cast<double>(M));
     mode = (l_max - L + log2(static_cast<double>(M)) + 12.0 < 126.0) ? 0 : 1;
   }
-  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, c.kap, c.gam, s);
-  if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode ? c.kap : nullptr, c.part, c.status, s);
-  if (e == cudaSuccess)
-    e = lsg::launch_combine(plan, d, c.xs, c.part, mode ? c.kap : nullptr, mode ? c.gam : nullptr, c.rows, per_n, s);
+  if (e == cudaSuccess) e = lsg::launch_prescale(plan, d, c.yl, mode, c.rec, s);
+  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, c.ls, c.gam, s);
+  if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode, c.ls, c.part, c.status, s);
+  if (e == cudaSuccess) e = lsg::launch_combine(plan, d, c.xs, c.part, mode, c.ls, c.gam, c.rows, per_n, s);
   if (e == cudaSuccess) e = lsg::launch_final_reduce(plan, d, c.rows, c.mom, s);
   double mom[LSGCPD_MOMENTS];
   double mu[3];

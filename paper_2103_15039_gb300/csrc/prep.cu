@@ -21,7 +21,7 @@ namespace lsg {
 namespace {
 
 constexpr int kStatThreads = 256;
-constexpr int kStatChunk = kStatThreads * 16;  // points per statistics CTA
+constexpr int kStatChunk = kStatThreads * 2;  // points per statistics CTA
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -136,6 +136,7 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, 
   double V = 1.0;
   for (int c = 0; c < 3; ++c) V *= fmax(s[c], 1e-2 * diag);
   st->diag = diag;
+  st->log2_pi = -log2(static_cast<double>(M));
   st->V = volume > 0.0 ? volume : V;
   st->sigma2_floor = floor_rel * diag * diag;
 }
@@ -433,24 +434,36 @@ __device__ void jacobi_sym3(double A[3][3], double V[3][3]) {
   }
 }
 
-__device__ __forceinline__ void write_record(float* rec, long long m, float ny0, float ny1, float ny2,
-                                             float a0, float a1, float a2, float l) {
-  const long long tile = m / kTile;
-  const int j = static_cast<int>(m % kTile);
+// Static planes 4-15 of a record slot and its yl entry (see internal.cuh).
+__device__ __forceinline__ void write_record(float* rec, float4* yl, long long slot, float y0, float y1, float y2,
+                                             float a0, float a1, float a2, float b0, float b1, float b2, float l) {
+  const long long tile = slot / kTile;
+  const int j = static_cast<int>(slot % kTile);
   float* r = rec + tile * kTileFloats + j;
-  const float v[kPlanes] = {ny0, ny1, ny2, a0, a1, a2, a0 * a0, a0 * a1, a0 * a2, a1 * a1, a1 * a2, a2 * a2, l};
+  const float v[12] = {a0, a1, a2, a0 * a0, a0 * a1, a0 * a2, a1 * a1, a1 * a2, a2 * a2, b0, b1, b2};
 #pragma unroll
-  for (int p = 0; p < kPlanes; ++p) r[p * kTile] = v[p];
+  for (int p = 0; p < 12; ++p) r[(4 + p) * kTile] = v[p];
+  yl[slot] = make_float4(y0, y1, y2, l);
 }
 
-__device__ __forceinline__ void pack_target(float* rec, long long slot, const float* y, const EmState* st,
-                                            double nx, double ny, double nz, double alpha, double log2_pi,
-                                            int alpha_norm) {
+__device__ __forceinline__ void write_padding(float* rec, float4* yl, long long slot) {
+  write_record(rec, yl, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+}
+
+// Record of target y (caller's frame) with normal n and penalty alpha: centred
+// coordinates, a = sqrt(alpha) n, b = Lambda y_c = y_c + (a . y_c) a (FP64, then FP32).
+__device__ __forceinline__ void pack_target(float* rec, float4* yl, long long slot, const float* y,
+                                            const EmState* st, double nx, double ny, double nz, double alpha,
+                                            double log2_pi, int alpha_norm) {
   const double sa = sqrt(alpha > 0.0 ? alpha : 0.0);
   const double l = log2_pi + (alpha_norm ? 0.5 * log2(1.0 + alpha) : 0.0);
-  write_record(rec, slot, static_cast<float>(-(y[0] - st->mu_y[0])), static_cast<float>(-(y[1] - st->mu_y[1])),
-               static_cast<float>(-(y[2] - st->mu_y[2])), static_cast<float>(sa * nx), static_cast<float>(sa * ny),
-               static_cast<float>(sa * nz), static_cast<float>(l));
+  const double c0 = y[0] - st->mu_y[0], c1 = y[1] - st->mu_y[1], c2 = y[2] - st->mu_y[2];
+  const double a0 = sa * nx, a1 = sa * ny, a2 = sa * nz;
+  const double ay = a0 * c0 + a1 * c1 + a2 * c2;
+  write_record(rec, yl, slot, static_cast<float>(c0), static_cast<float>(c1), static_cast<float>(c2),
+               static_cast<float>(a0), static_cast<float>(a1), static_cast<float>(a2),
+               static_cast<float>(c0 + ay * a0), static_cast<float>(c1 + ay * a1), static_cast<float>(c2 + ay * a2),
+               static_cast<float>(l));
 }
 
 // grid = (largest tile count, P), kTile threads: target m = tile * kTile + tid of
@@ -461,8 +474,9 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
                                                          const int* __restrict__ idx, int k, double alpha_max,
                                                          double lambda, int alpha_norm,
                                                          const EmState* __restrict__ st_all,
-                                                         float* __restrict__ rec, float* __restrict__ normals,
-                                                         float* __restrict__ kappa, float* __restrict__ alpha_out) {
+                                                         float* __restrict__ rec, float4* __restrict__ yl,
+                                                         float* __restrict__ normals, float* __restrict__ kappa,
+                                                         float* __restrict__ alpha_out) {
   const int pair = blockIdx.y;
   const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
   if (static_cast<int>(blockIdx.x) >= t1 - t0) return;
@@ -471,7 +485,7 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
   const long long m = static_cast<long long>(blockIdx.x) * kTile + threadIdx.x;
   const long long slot = static_cast<long long>(t0 + blockIdx.x) * kTile + threadIdx.x;
   if (m >= M) {
-    write_record(rec, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    write_padding(rec, yl, slot);
     return;
   }
   const long long gm = m0 + m;
@@ -511,7 +525,7 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
   }
   double a = kap > 0.0 ? alpha_max * tanh(0.5 * lambda * (1.0 / kap - 3.0)) : alpha_max;
   if (a < 0.0) a = 0.0;
-  pack_target(rec, slot, Y + 3 * gm, st_all + pair, n0, n1, n2, a, -log2(static_cast<double>(M)), alpha_norm);
+  pack_target(rec, yl, slot, Y + 3 * gm, st_all + pair, n0, n1, n2, a, st_all[pair].log2_pi, alpha_norm);
   if (normals) {
     normals[3 * gm] = static_cast<float>(n0);
     normals[3 * gm + 1] = static_cast<float>(n1);
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y
                                                      const int* __restrict__ tab, Geo g,
                                                      const float* __restrict__ normals, const float* __restrict__ alpha,
                                                      int alpha_norm, const EmState* __restrict__ st_all,
-                                                     float* __restrict__ rec) {
+                                                     float* __restrict__ rec, float4* __restrict__ yl) {
   const int pair = blockIdx.y;
   const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
   if (static_cast<int>(blockIdx.x) >= t1 - t0) return;
@@ -534,12 +548,12 @@ __global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y
   const long long m = static_cast<long long>(blockIdx.x) * kTile + threadIdx.x;
   const long long slot = static_cast<long long>(t0 + blockIdx.x) * kTile + threadIdx.x;
   if (m >= M) {
-    write_record(rec, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -INFINITY);
+    write_padding(rec, yl, slot);
     return;
   }
   const long long gm = m0 + m;
-  pack_target(rec, slot, Y + 3 * gm, st_all + pair, normals[3 * gm], normals[3 * gm + 1], normals[3 * gm + 2],
-              alpha[gm], -log2(static_cast<double>(M)), alpha_norm);
+  pack_target(rec, yl, slot, Y + 3 * gm, st_all + pair, normals[3 * gm], normals[3 * gm + 1], normals[3 * gm + 2],
+              alpha[gm], st_all[pair].log2_pi, alpha_norm);
 }
 
 }  // namespace
@@ -600,18 +614,18 @@ cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, 
 }
 
 cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
-                            double alpha_max, double lambda, int alpha_norm, float* rec, float* normals,
-                            float* kappa, float* alpha, cudaStream_t s) {
+                            double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
+                            float* normals, float* kappa, float* alpha, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
   geometry_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, idx, k, alpha_max, lambda, alpha_norm, d.st, rec,
-                                         normals, kappa, alpha);
+                                         yl, normals, kappa, alpha);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals, const float* alpha,
-                        int alpha_norm, float* rec, cudaStream_t s) {
+                        int alpha_norm, float* rec, float4* yl, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
-  pack_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, normals, alpha, alpha_norm, d.st, rec);
+  pack_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, normals, alpha, alpha_norm, d.st, rec, yl);
   return cudaGetLastError();
 }
 
