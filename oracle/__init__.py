@@ -42,6 +42,8 @@ def lib():
         ip = C.POINTER(C.c_int32)
         i64 = C.c_int64
         L.oracle_knn.argtypes = [fp, i64, C.c_int32, C.c_int32, ip]
+        L.oracle_knn_grid.argtypes = [fp, i64, C.c_int32, C.c_int32, ip]
+        L.oracle_knn_subset.argtypes = [fp, i64, C.POINTER(C.c_int64), i64, C.c_int32, C.c_int32, ip]
         L.oracle_jacobi3.argtypes = [dp, dp, dp]
         L.oracle_penalty.argtypes = [C.c_double] * 3
         L.oracle_penalty.restype = C.c_double
@@ -78,13 +80,30 @@ def _p(a, t):
     return a.ctypes.data_as(C.POINTER(t))
 
 
-def knn(Y, k, threads=0):
+def knn(Y, k, threads=0, method="auto"):
+    """k nearest targets of every target (self included, ties to the lower index).
+    method: "brute" (O(M^2)), "grid" (exact uniform-grid search, same result) or
+    "auto" (grid above 20,000 points)."""
     Y = _f32(Y)
     M = len(Y)
     idx = np.empty((M, k), dtype=np.int32)
-    rc = lib().oracle_knn(_p(Y, C.c_float), M, k, threads, _p(idx, C.c_int32))
+    use_grid = method == "grid" or (method == "auto" and M > 20000)
+    fn = lib().oracle_knn_grid if use_grid else lib().oracle_knn
+    rc = fn(_p(Y, C.c_float), M, k, threads, _p(idx, C.c_int32))
     if rc:
         raise ValueError("oracle_knn: invalid arguments")
+    return idx
+
+
+def knn_rows(Y, queries, k, threads=0):
+    """Brute-force k nearest targets of the listed queries (the corresponding rows of knn)."""
+    Y = _f32(Y)
+    q = np.ascontiguousarray(queries, dtype=np.int64)
+    idx = np.empty((len(q), k), dtype=np.int32)
+    rc = lib().oracle_knn_subset(_p(Y, C.c_float), len(Y), _p(q, C.c_int64), len(q), k, threads,
+                                 _p(idx, C.c_int32))
+    if rc:
+        raise ValueError("oracle_knn_subset: invalid arguments")
     return idx
 
 
@@ -116,7 +135,7 @@ def local_geometry(Y, idx, alpha_max, lam):
 
 
 def preprocess(Y, k, alpha_max, lam, threads=0):
-    idx = knn(Y, k, threads)
+    idx = knn(Y, k, threads)  # grid search above 20,000 targets (same result)
     nrm, kap, alp = local_geometry(Y, idx, alpha_max, lam)
     return dict(idx=idx, normals=nrm, kappa=kap, alpha=alp)
 

@@ -432,6 +432,123 @@ int oracle_knn(const float* Y, int64_t M, int32_t k, int32_t threads, int32_t* i
   return 0;
 }
 
+// Brute-force k nearest targets of the listed queries only (rows of oracle_knn).
+int oracle_knn_subset(const float* Y, int64_t M, const int64_t* queries, int64_t nq, int32_t k, int32_t threads,
+                      int32_t* idx) {
+  if (M <= 0 || k <= 0 || k > M || nq < 0) return 1;
+  for (int64_t i = 0; i < nq; ++i)
+    if (queries[i] < 0 || queries[i] >= M) return 1;
+  parallel_for(nq, thread_count(threads), [&](int64_t lo, int64_t hi, int) {
+    std::vector<std::pair<float, int32_t>> d(static_cast<size_t>(M));
+    for (int64_t i = lo; i < hi; ++i) {
+      const int64_t q = queries[i];
+      float qx = Y[3 * q], qy = Y[3 * q + 1], qz = Y[3 * q + 2];
+      for (int64_t m = 0; m < M; ++m) {
+        float dx = qx - Y[3 * m], dy = qy - Y[3 * m + 1], dz = qz - Y[3 * m + 2];
+        d[m] = {std::fmaf(dz, dz, std::fmaf(dy, dy, dx * dx)), static_cast<int32_t>(m)};
+      }
+      std::partial_sort(d.begin(), d.begin() + k, d.end());
+      for (int j = 0; j < k; ++j) idx[i * k + j] = d[j].second;
+    }
+  });
+  return 0;
+}
+
+// The same k nearest neighbours as oracle_knn (same FP32 distances, same
+// (distance, index) order), found through a uniform grid so that clouds of
+// 10^5..10^6 points finish in seconds.  Cells are visited in growing cubic
+// shells around the query's cell; the search stops once the k-th distance is
+// below the squared distance from the query to the boundary of the visited
+// cube (with a relative margin of 1e-5, far above FP32 rounding of a squared
+// distance), so every point that could enter or tie the list was examined.
+int oracle_knn_grid(const float* Y, int64_t M, int32_t k, int32_t threads, int32_t* idx) {
+  if (M <= 0 || k <= 0 || k > M) return 1;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t m = 0; m < M; ++m)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], static_cast<double>(Y[3 * m + a]));
+      hi[a] = std::max(hi[a], static_cast<double>(Y[3 * m + a]));
+    }
+  double diag = 0;
+  for (int a = 0; a < 3; ++a) diag += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+  diag = std::sqrt(diag);
+  // cell edge for about k points per cell on a surface-like cloud; at most 256 cells per axis
+  double h = diag * std::sqrt(static_cast<double>(k) / static_cast<double>(M));
+  int64_t dim[3];
+  for (int pass = 0; pass < 64; ++pass) {
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      dim[a] = h > 0 ? static_cast<int64_t>(std::floor((hi[a] - lo[a]) / h)) + 1 : 1;
+      if (dim[a] > 256) ok = false;
+    }
+    if (ok) break;
+    h *= 1.5;
+  }
+  if (!(h > 0)) h = 1.0;
+  const int64_t ncell = dim[0] * dim[1] * dim[2];
+  auto cell_of = [&](double v, int a) {
+    int64_t c = static_cast<int64_t>(std::floor((v - lo[a]) / h));
+    return std::min<int64_t>(std::max<int64_t>(c, 0), dim[a] - 1);
+  };
+  std::vector<int64_t> start(static_cast<size_t>(ncell + 1), 0);
+  std::vector<int64_t> cid(static_cast<size_t>(M));
+  for (int64_t m = 0; m < M; ++m) {
+    cid[m] = (cell_of(Y[3 * m + 2], 2) * dim[1] + cell_of(Y[3 * m + 1], 1)) * dim[0] + cell_of(Y[3 * m], 0);
+    ++start[cid[m] + 1];
+  }
+  for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+  std::vector<int32_t> order(static_cast<size_t>(M));
+  {
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t m = 0; m < M; ++m) order[fill[cid[m]]++] = static_cast<int32_t>(m);
+  }
+  parallel_for(M, thread_count(threads), [&](int64_t q0, int64_t q1, int) {
+    std::vector<std::pair<float, int32_t>> best;
+    for (int64_t q = q0; q < q1; ++q) {
+      const float qx = Y[3 * q], qy = Y[3 * q + 1], qz = Y[3 * q + 2];
+      const int64_t c[3] = {cell_of(qx, 0), cell_of(qy, 1), cell_of(qz, 2)};
+      best.clear();
+      for (int64_t r = 0;; ++r) {
+        for (int64_t z = c[2] - r; z <= c[2] + r; ++z) {
+          if (z < 0 || z >= dim[2]) continue;
+          for (int64_t y = c[1] - r; y <= c[1] + r; ++y) {
+            if (y < 0 || y >= dim[1]) continue;
+            for (int64_t x = c[0] - r; x <= c[0] + r; ++x) {
+              if (x < 0 || x >= dim[0]) continue;
+              const bool shell = std::llabs(z - c[2]) == r || std::llabs(y - c[1]) == r || std::llabs(x - c[0]) == r;
+              if (!shell) continue;
+              const int64_t cc = (z * dim[1] + y) * dim[0] + x;
+              for (int64_t j = start[cc]; j < start[cc + 1]; ++j) {
+                const int32_t m = order[j];
+                float dx = qx - Y[3 * m], dy = qy - Y[3 * m + 1], dz = qz - Y[3 * m + 2];
+                best.push_back({std::fmaf(dz, dz, std::fmaf(dy, dy, dx * dx)), m});
+              }
+            }
+          }
+        }
+        const bool all = c[0] - r <= 0 && c[1] - r <= 0 && c[2] - r <= 0 && c[0] + r >= dim[0] - 1 &&
+                         c[1] + r >= dim[1] - 1 && c[2] + r >= dim[2] - 1;
+        if (static_cast<int64_t>(best.size()) >= k) {
+          std::partial_sort(best.begin(), best.begin() + k, best.end());
+          best.resize(static_cast<size_t>(k));
+          // distance from the query to the boundary of the visited cube of cells
+          double bound = 1e300;
+          const double qv[3] = {qx, qy, qz};
+          for (int a = 0; a < 3; ++a) {
+            if (c[a] - r > 0) bound = std::min(bound, qv[a] - (lo[a] + (c[a] - r) * h));
+            if (c[a] + r < dim[a] - 1) bound = std::min(bound, (lo[a] + (c[a] + r + 1) * h) - qv[a]);
+          }
+          if (all || (bound > 0 && static_cast<double>(best[k - 1].first) < bound * bound * (1.0 - 1e-5))) break;
+        } else if (all) {
+          break;
+        }
+      }
+      for (int j = 0; j < k; ++j) idx[q * k + j] = best[j].second;
+    }
+  });
+  return 0;
+}
+
 // Eigen-decomposition exposed for the tests (ascending eigenvalues, eigenvectors in columns).
 void oracle_jacobi3(const double* C, double* evals, double* evecs) { jacobi3(C, evals, evecs); }
 
@@ -739,7 +856,10 @@ int oracle_register(const float* X, int64_t N, const float* Y, int64_t M, const 
     return 1;
   int k = p->knn_k;
   std::vector<int32_t> idx(static_cast<size_t>(M * k));
-  oracle_knn(Y, M, k, p->threads, idx.data());
+  if (M > 20000)
+    oracle_knn_grid(Y, M, k, p->threads, idx.data());
+  else
+    oracle_knn(Y, M, k, p->threads, idx.data());
   std::vector<double> nrm(static_cast<size_t>(3 * M)), kap(static_cast<size_t>(M)),
       alp(static_cast<size_t>(M));
   oracle_local_geometry(Y, M, idx.data(), k, p->alpha_max, p->lambda, nrm.data(), kap.data(),

@@ -264,6 +264,30 @@ def test_knn_ties_go_to_lower_index():
     assert list(idx[0]) == [0, 1, 2]
 
 
+@pytest.mark.parametrize("shape", ["uniform", "lattice", "plane", "clusters", "duplicates"])
+def test_grid_knn_equals_bruteforce(shape):
+    """The grid search is only a faster route to the brute-force result: every
+    row, including exact ties on a lattice and duplicated points, is identical."""
+    rng = np.random.default_rng(11)
+    Y = {"uniform": rng.uniform(-1, 1, (2500, 3)),
+         "lattice": np.stack(np.meshgrid(*[np.arange(11)] * 3), -1).reshape(-1, 3) * 0.25,
+         "plane": np.c_[rng.uniform(0, 1, (2000, 2)), np.zeros(2000)],
+         "clusters": np.concatenate([rng.normal(c, 0.01, (400, 3)) for c in rng.uniform(-5, 5, (5, 3))]),
+         "duplicates": np.repeat(rng.uniform(0, 1, (250, 3)), 4, axis=0)}[shape].astype(np.float32)
+    for k in (1, 10, 32):
+        np.testing.assert_array_equal(oracle.knn(Y, k, method="grid"), oracle.knn(Y, k, method="brute"))
+
+
+def test_grid_knn_rows_on_a_large_scan():
+    """100k-point LiDAR-shaped cloud: sampled rows of the grid search against
+    brute force over all points."""
+    c = synth.lidar_pair()
+    Y = c["Y"]
+    g = oracle.knn(Y, 10, method="grid")
+    q = np.random.default_rng(5).choice(len(Y), 60, replace=False)
+    np.testing.assert_array_equal(g[q], oracle.knn_rows(Y, q, 10))
+
+
 def test_planar_neighbourhood_gives_zero_variation_and_max_penalty():
     rng = np.random.default_rng(4)
     pts = np.zeros((300, 3))
