@@ -170,6 +170,13 @@ def profile_traffic():
     return prof.get("dram_bytes_per_launch")
 
 
+def plan_obj(ctx):
+    """The E-step plan of the last call (sources per thread chosen by the autotuner)."""
+    info = ctx.plan_info()
+    return {"sources_per_thread": info["sources_per_thread"], "block": info["block"], "ctas": info["ctas"],
+            "autotuned": info["tuned"], "tune_ms": {str(k): round(v, 5) for k, v in info["tune_ms"].items()}}
+
+
 def cpu_baseline(c, got, iters, budget_s=40.0):
     """The FP64 oracle timed on this host's cores on the same pair.
 
@@ -313,7 +320,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4),
                    "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
-           "mode": got["mode"], "iters_run": iters_run}
+           "mode": got["mode"], "iters_run": iters_run, "e_step_plan": plan_obj(ctx)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, err = cpu_baseline(c, got, iters_run)
         out["cpu_baseline"] = cb
@@ -439,6 +446,7 @@ def run_batch(args):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4), "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches, "iters_run": iters_run,
+           "e_step_plan": plan_obj(ctx),
            "per_pair_form": {"value": pp_pairs / (pp_ms / 1e3), "unit": UNIT, "ms_per_step": round(pp_ms, 3),
                              "calls": P, "batched_speedup": round((pp_ms / pp_pairs) / (ms / pairs_per_step), 3)}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

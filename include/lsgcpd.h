@@ -177,6 +177,27 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const 
                               const lsgcpd_params* p, lsgcpd_result* out, double* trace,
                               void* stream);
 
+/* Autotuning of the E step's source tile (on by default).  The hot kernel can
+ * give each thread 4, 2 or 1 sources (source blocks of 1024, 256 or 128
+ * sources): fewer sources per thread waste less padding on small or uneven
+ * pairs, more share each target tile among more sources.  With autotuning on,
+ * the first lsgcpd_register / lsgcpd_register_batch call for a problem shape
+ * (the list of N_i, M_i) whose E step has at most 1.5e10 pairs times one
+ * E-step launch of each variant on the caller's data (after a warm-up launch)
+ * and keeps the fastest; later calls with the same shape reuse the choice.
+ * With it off (or above the size limit) a fixed rule chooses.  The choice
+ * changes only the FP32 summation order, so results within one context are
+ * reproducible; two contexts can differ at FP32 rounding level.  The paper
+ * has no counterpart (a GB300 scheduling choice).  enable: 0 or 1. */
+lsgcpd_status lsgcpd_set_autotune(lsgcpd_ctx* ctx, int enable);
+
+/* The plan of the last registration call: info[0] sources per thread,
+ * info[1] sources per block, info[2] E-step CTAs, info[3] = 1 if the source
+ * tile was chosen by measurement (this call or an earlier one with the same
+ * shape).  tune_ms (may be NULL): measured ms per E-step launch for 4, 2 and 1
+ * sources per thread (0 where not measured).  Host memory. */
+lsgcpd_status lsgcpd_plan_info(const lsgcpd_ctx* ctx, int32_t info[4], double tune_ms[3]);
+
 /* Largest num_pairs of lsgcpd_register_batch. */
 #define LSGCPD_MAX_PAIRS 65535
 

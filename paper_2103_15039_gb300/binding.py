@@ -80,6 +80,10 @@ def lib():
         L.lsgcpd_register_batch.argtypes = [vp, C.c_int32, fp, C.POINTER(i64), fp, C.POINTER(i64),
                                             C.POINTER(Params), dp, dp, dp, C.POINTER(C.c_int32), dp, vp]
         L.lsgcpd_register_batch.restype = C.c_int
+        L.lsgcpd_set_autotune.argtypes = [vp, C.c_int]
+        L.lsgcpd_set_autotune.restype = C.c_int
+        L.lsgcpd_plan_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
+        L.lsgcpd_plan_info.restype = C.c_int
         L.lsgcpd_estep_noalloc.argtypes = [fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
                                            C.c_double, dp, fp, vp]
         L.lsgcpd_estep_noalloc.restype = C.c_int
@@ -289,6 +293,19 @@ def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=N
     return out
 
 
+def lsgcpd_set_autotune(ctx, enable):
+    _check(ctx, lib().lsgcpd_set_autotune(ctx, 1 if enable else 0))
+
+
+def lsgcpd_plan_info(ctx):
+    info = np.zeros(4, dtype=np.int32)
+    ms = np.zeros(3)
+    _check(ctx, lib().lsgcpd_plan_info(ctx, info.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       ms.ctypes.data_as(C.POINTER(C.c_double))))
+    return dict(sources_per_thread=int(info[0]), block=int(info[1]), ctas=int(info[2]), tuned=bool(info[3]),
+                tune_ms={4: ms[0], 2: ms[1], 1: ms[2]})
+
+
 def lsgcpd_set_timing(ctx, enable):
     lib().lsgcpd_set_timing(ctx, 1 if enable else 0)
 
@@ -331,6 +348,12 @@ class Context:
 
     def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None):
         return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream)
+
+    def set_autotune(self, enable):
+        lsgcpd_set_autotune(self.handle, enable)
+
+    def plan_info(self):
+        return lsgcpd_plan_info(self.handle)
 
     def set_timing(self, enable):
         lsgcpd_set_timing(self.handle, enable)

@@ -17,6 +17,8 @@ using namespace lsg;
 namespace {
 
 constexpr int kMaxK = 32;
+// problems up to this many pairs per E step (about 12 ms) are autotuned on first sight
+constexpr double kTuneMaxPairs = 1.5e10;
 
 template <class T>
 struct DevBuf {
@@ -64,6 +66,17 @@ struct lsgcpd_ctx {
   double last_timing[5] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   int64_t h2d_bytes = 0, d2h_bytes = 0;
+  // autotuning of the E step's source tile (sources per thread), per problem shape
+  int autotune = 1;
+  struct Tuned {
+    std::vector<long long> sizes;
+    int S;
+    double ms[3];  // measured ms per E-step launch for S = 4, 2, 1 (0: not measured)
+  };
+  std::vector<Tuned> tuned;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  int32_t last_plan[4] = {0, 0, 0, 0};  // S, SB, grid, chosen by measurement
+  double last_tune_ms[3] = {0, 0, 0};
 };
 
 namespace {
@@ -314,11 +327,24 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     if (k > M[i]) return fail(c, LSGCPD_EINVAL, "knn_k must not exceed the target count of any pair");
   LSG_CUDA(enter(c, stream), "stream");
   const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
-  const BatchPlan plan = plan_batch(N, M, c->num_sms, 0);
-  const Geo& g = plan.g;
-  const long long Ntot = plan.off64[P], Mtot = plan.off64[2 * P + 1];
   const int iters = p->max_iters;
+  // source tile: measured once per problem shape (cached), else the plan's heuristic
+  std::vector<long long> skey = N;
+  skey.insert(skey.end(), M.begin(), M.end());
+  const lsgcpd_ctx::Tuned* hit = nullptr;
+  if (c->autotune)
+    for (const auto& t : c->tuned)
+      if (t.sizes == skey) hit = &t;
+  double pairs = 0;
+  for (int i = 0; i < P; ++i) pairs += static_cast<double>(N[i]) * static_cast<double>(M[i]);
+  const bool tune = c->autotune && iters > 0 && !hit && pairs <= kTuneMaxPairs;
+  BatchPlan plan = plan_batch(N, M, c->num_sms, hit ? hit->S : 0);
+  std::vector<BatchPlan> cands;
+  if (tune)
+    for (int S : {4, 2, 1}) cands.push_back(S == plan.g.S ? plan : plan_batch(N, M, c->num_sms, S));
+  const long long Ntot = plan.off64[P], Mtot = plan.off64[2 * P + 1];
   lsgcpd_status rs = reserve(c, plan, k, iters, !xd || !yd);
+  for (size_t i = 0; i < cands.size() && rs == LSGCPD_OK; ++i) rs = reserve(c, cands[i], k, iters, !xd || !yd);
   if (rs != LSGCPD_OK) return rs;
   cudaStream_t s = c->stream;
   const Dev d = dev_of(c);
@@ -342,7 +368,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   LSG_CUDA(check_finite(Yd, Mtot * 3, c->status, s), "check");
   const DevParams dp = dev_params(p);
   LSG_CUDA(launch_init(plan, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
-  const int splits = knn_splits(g, c->num_sms);
+  const int splits = knn_splits(plan.g, c->num_sms);
   LSG_CUDA(launch_knn(plan, d, Yd, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, s), "knn");
   LSG_CUDA(launch_geometry(plan, d, Yd, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
                            c->yl.p, nullptr, nullptr, nullptr, s),
@@ -363,6 +389,43 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   // per-source shifts also when l_m varies (the uniform-shift moments assume one l)
   int mode = p->include_alpha_norm ? 1 : 0;
   for (int i = 0; i < P; ++i) mode |= choose_mode(p->w, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
+  if (tune) {
+    // time one E-step launch (after a warm-up launch) for every source tile and keep the fastest;
+    // the target records do not depend on it, the source layout and the EM state are rebuilt
+    lsgcpd_ctx::Tuned rec{skey, plan.g.S, {0, 0, 0}};
+    double best = 1e300;
+    for (const BatchPlan& pc : cands) {
+      LSG_CUDA(upload_plan(c, pc, s), "plan");
+      LSG_CUDA(launch_init(pc, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
+      LSG_CUDA(launch_prescale(pc, d, c->yl.p, mode, c->rec.p, s), "prescale");
+      if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s), "shift");
+      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
+      LSG_CUDA(cudaEventRecord(c->tune_ev[0], s), "event");
+      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
+      LSG_CUDA(cudaEventRecord(c->tune_ev[1], s), "event");
+      LSG_CUDA(cudaEventSynchronize(c->tune_ev[1]), "sync");
+      const double ms = elapsed_ms(c->tune_ev[0], c->tune_ev[1]);
+      rec.ms[pc.g.S == 4 ? 0 : (pc.g.S == 2 ? 1 : 2)] = ms;
+      if (ms > 0 && ms < best) {
+        best = ms;
+        rec.S = pc.g.S;
+      }
+      launches += (mode ? 6 : 5) + 2;
+    }
+    for (const BatchPlan& pc : cands)
+      if (pc.g.S == rec.S) plan = pc;
+    c->tuned.push_back(rec);
+    hit = &c->tuned.back();
+    LSG_CUDA(upload_plan(c, plan, s), "plan");
+    LSG_CUDA(launch_init(plan, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
+    launches += 4;
+  }
+  const Geo& g = plan.g;
+  c->last_plan[0] = g.S;
+  c->last_plan[1] = g.SB;
+  c->last_plan[2] = g.grid;
+  c->last_plan[3] = hit ? 1 : 0;
+  for (int i = 0; i < 3; ++i) c->last_tune_ms[i] = hit ? hit->ms[i] : 0.0;
   if (iters > 0) {
     GraphKey key;
     key.sizes = N;
@@ -499,7 +562,8 @@ lsgcpd_status lsgcpd_create(lsgcpd_ctx** out, int device, int64_t max_N, int64_t
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t_begin) != cudaSuccess || cudaEventCreate(&c->t_prep) != cudaSuccess ||
-      cudaEventCreate(&c->t_end) != cudaSuccess) {
+      cudaEventCreate(&c->t_end) != cudaSuccess || cudaEventCreate(&c->tune_ev[0]) != cudaSuccess ||
+      cudaEventCreate(&c->tune_ev[1]) != cudaSuccess) {
     cudaGetLastError();
     return bail(LSGCPD_ECUDA);
   }
@@ -534,7 +598,7 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
     for (int i = 0; i < 4 * c->t_iter_cap; ++i) cudaEventDestroy(c->t_iter[i]);
     delete[] c->t_iter;
   }
-  cudaEvent_t evs[] = {c->ev_in, c->ev_out, c->t_begin, c->t_prep, c->t_end};
+  cudaEvent_t evs[] = {c->ev_in, c->ev_out, c->t_begin, c->t_prep, c->t_end, c->tune_ev[0], c->tune_ev[1]};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -547,6 +611,20 @@ const char* lsgcpd_last_error(const lsgcpd_ctx* c) { return c ? c->err.c_str() :
 lsgcpd_status lsgcpd_set_timing(lsgcpd_ctx* c, int enable) {
   if (!c) return LSGCPD_EINVAL;
   c->timing = enable ? 1 : 0;
+  return LSGCPD_OK;
+}
+
+lsgcpd_status lsgcpd_set_autotune(lsgcpd_ctx* c, int enable) {
+  if (!c) return LSGCPD_EINVAL;
+  c->autotune = enable ? 1 : 0;
+  return LSGCPD_OK;
+}
+
+lsgcpd_status lsgcpd_plan_info(const lsgcpd_ctx* c, int32_t info[4], double tune_ms[3]) {
+  if (!c || !info) return LSGCPD_EINVAL;
+  for (int i = 0; i < 4; ++i) info[i] = c->last_plan[i];
+  if (tune_ms)
+    for (int i = 0; i < 3; ++i) tune_ms[i] = c->last_tune_ms[i];
   return LSGCPD_OK;
 }
 

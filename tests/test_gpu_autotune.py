@@ -1,0 +1,79 @@
+"""Autotuning of the E step's source tile (sources per thread) through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_15039_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _diag(Y):
+    Y = np.asarray(Y, dtype=np.float64)
+    return float(np.linalg.norm(Y.max(0) - Y.min(0)))
+
+
+def _concat(pairs):
+    X = np.concatenate([p["X"] for p in pairs]).astype(np.float32)
+    Y = np.concatenate([p["Y"] for p in pairs]).astype(np.float32)
+    n_off = np.concatenate([[0], np.cumsum([len(p["X"]) for p in pairs])])
+    m_off = np.concatenate([[0], np.cumsum([len(p["Y"]) for p in pairs])])
+    return X, n_off, Y, m_off
+
+
+def test_autotune_measures_every_tile_and_keeps_the_fastest():
+    ctx = binding.Context(0, 4096, 4096)
+    try:
+        c = synth.sphere_plane_pair(seed=51, n=3000, m=2500)
+        p = binding.default_params(max_iters=5)
+        a = ctx.register(c["X"], c["Y"], p)
+        info = ctx.plan_info()
+        assert info["tuned"]
+        ms = info["tune_ms"]
+        assert all(v > 0 for v in ms.values())
+        assert ms[info["sources_per_thread"]] == min(ms.values())
+        assert info["block"] == {4: 1024, 2: 256, 1: 128}[info["sources_per_thread"]]
+        # the second call reuses the choice and reproduces the result bit for bit
+        b = ctx.register(c["X"], c["Y"], p)
+        assert ctx.plan_info()["tuned"] and ctx.plan_info()["tune_ms"] == ms
+        np.testing.assert_array_equal(a["R"], b["R"])
+        np.testing.assert_array_equal(a["t"], b["t"])
+    finally:
+        ctx.close()
+
+
+def test_every_source_tile_gives_the_oracle_result():
+    """Whatever tile the tuner picks, the registration meets the FP64 bar."""
+    c = synth.sphere_plane_pair(seed=52, n=1100, m=900)
+    ref = oracle.register(c["X"], c["Y"], max_iters=20)
+    ctx = binding.Context(0, 2048, 2048)
+    try:
+        ctx.set_autotune(False)
+        p = binding.default_params(max_iters=20)
+        got = ctx.register(c["X"], c["Y"], p)
+        assert not ctx.plan_info()["tuned"]
+        ctx.set_autotune(True)
+        tuned = ctx.register(c["X"], c["Y"], p)
+        for g in (got, tuned):
+            assert oracle.rotation_error(g["R"], ref["R"]) < 1e-4
+            assert np.linalg.norm(g["t"] - ref["t"]) / _diag(c["Y"]) < 1e-5
+    finally:
+        ctx.close()
+
+
+def test_autotuned_batch_matches_untuned():
+    pairs = synth.batch_pairs(num_pairs=12, n_lo=100, n_hi=3000)
+    X, n_off, Y, m_off = _concat(pairs)
+    p = binding.default_params(max_iters=15)
+    ctx = binding.Context(0, 4096, 4096)
+    try:
+        ctx.set_autotune(False)
+        a = ctx.register_batch(X, n_off, Y, m_off, p)
+        ctx.set_autotune(True)
+        b = ctx.register_batch(X, n_off, Y, m_off, p)
+        assert ctx.plan_info()["tuned"]
+        for i, c in enumerate(pairs):
+            assert oracle.rotation_error(a["R"][i], b["R"][i]) < 1e-4
+            assert np.linalg.norm(a["t"][i] - b["t"][i]) / _diag(c["Y"]) < 1e-5
+    finally:
+        ctx.close()
