@@ -29,6 +29,8 @@ class OracleParams(C.Structure):
         ("init_t", C.c_double * 3), ("newton_tol", C.c_double), ("sigma2_floor_rel", C.c_double),
         ("knn_k", C.c_int32), ("max_iters", C.c_int32), ("include_alpha_norm", C.c_int32),
         ("newton_max", C.c_int32), ("threads", C.c_int32), ("pad_", C.c_int32),
+        ("eta", C.c_double), ("cf_threshold", C.c_double), ("nll_tol", C.c_double),
+        ("phi_x", C.POINTER(C.c_float)), ("phi_y", C.POINTER(C.c_float)),
     ]
 
 
@@ -62,6 +64,8 @@ def lib():
         L.oracle_mstep.argtypes = [dp, fp, i64, dp, dp, C.c_int32, C.c_double, dp, dp, dp, dp, ip]
         L.oracle_register.argtypes = [fp, i64, fp, i64, C.POINTER(OracleParams), dp, dp, dp, ip, dp,
                                       dp, dp]
+        L.oracle_w_from_eta.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp, i64, C.c_int32]
+        L.oracle_w_from_eta.restype = C.c_double
         _lib = L
     return _lib
 
@@ -252,6 +256,9 @@ def default_params(**kw):
     p.include_alpha_norm = 0
     p.newton_max = 20
     p.threads = 0
+    p.eta = 0.0
+    p.cf_threshold = 0.0
+    p.nll_tol = 0.0
     for key, val in kw.items():
         if key == "init_R":
             for i, v in enumerate(np.asarray(val, dtype=np.float64).ravel()):
@@ -264,10 +271,27 @@ def default_params(**kw):
     return p
 
 
-def register(X, Y, params=None, **kw):
-    """Full LSG-CPD registration; returns dict(R, t, sigma2, iters, trace, normals, alpha, rc)."""
+def w_from_eta(eta, V, sigma2, alpha=None, pi_m=None, M=None, include_alpha_norm=False):
+    """w_max of Sec. 3.2 (reading R14)."""
+    a = None if alpha is None else _f64(alpha)
+    pi = None if pi_m is None else _f64(pi_m)
+    M = M if M is not None else len(a if a is not None else pi)
+    return lib().oracle_w_from_eta(float(eta), float(V), float(sigma2), _p(a, C.c_double), _p(pi, C.c_double),
+                                   int(M), int(include_alpha_norm))
+
+
+def register(X, Y, params=None, phi_x=None, phi_y=None, **kw):
+    """Full LSG-CPD registration; returns dict(R, t, sigma2, iters, trace, normals, alpha, rc).
+    phi_x / phi_y: optional per-point confidences of Sec. 3.3 (with cf_threshold, eta in kw)."""
     p = params if params is not None else default_params(**kw)
     X, Y = _f32(X), _f32(Y)
+    keep = []
+    if phi_x is not None:
+        keep.append(_f32(phi_x))
+        p.phi_x = _p(keep[-1], C.c_float)
+    if phi_y is not None:
+        keep.append(_f32(phi_y))
+        p.phi_y = _p(keep[-1], C.c_float)
     Ro = np.empty(9)
     to = np.empty(3)
     s2 = C.c_double(0)

@@ -32,6 +32,16 @@
 //       the Newton step nor its minimiser.  Gradient and Hessian follow Eqs.
 //       (11)-(12) with the same scaling.
 //   R9  se(3) basis order: E1..E3 rotations about x, y, z; E4..E6 translations.
+//   R14 Outlier weight from the outlier ratio eta (Sec. 3.2): w0 = w_max =
+//       eta V S / ((1 - eta) + eta V S), S = sum_m pi(m) c_m, with c_m the peak
+//       of component m (R1) evaluated once, at sigma^2_0.
+//   R15 Confidence filtering (Sec. 3.3): pi(m) = phi(y_m) / sum phi(y),
+//       w_n = 1 - (1 - w0) phi(x_n); truncation removes the points with
+//       phi < threshold from X and Y before anything else (neighbourhoods,
+//       sigma^2_0, V and the priors are those of the kept points).
+//   R16 Termination on the log-likelihood (Eq. (4)): after the E step of an
+//       iteration i >= 1, if |NLL_i - NLL_{i-1}| <= nll_tol |NLL_i| the M step of
+//       that iteration still runs and EM stops.
 //
 // Build:  g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared -pthread
 // (-ffp-contract=off keeps every product separately rounded, so the only fused
@@ -411,6 +421,11 @@ struct oracle_params {
   int32_t newton_max;
   int32_t threads;      // 0 = all hardware threads
   int32_t pad_;
+  double eta;           // > 0: w0 = w_max of Sec. 3.2 at sigma^2_0 (reading R14); else w
+  double cf_threshold;  // Sec. 3.3 truncation: points with phi < cf_threshold are dropped (R15)
+  double nll_tol;       // > 0: stop when the NLL of Eq. (4) changes by <= nll_tol relative (R16)
+  const float* phi_x;   // confidence phi of every source (Sec. 3.3), NULL = 1
+  const float* phi_y;   // confidence phi of every target, NULL = 1
 };
 
 // --- kNN (reading R5): k nearest targets of every target, FP32 distance decisions.
@@ -849,11 +864,52 @@ int oracle_mstep(const double* stats, const float* X, int64_t N, const double* R
 // E step -> Newton M step -> sigma^2 update.  Per-iteration trace (8 doubles):
 // sigma2 after the update, N_P, Q_d(g_new), newton_iters, damped, motion, NLL at
 // the E step, outlier mass.  Returns 0, or 2 if N_P vanished.
+// Sec. 3.2 (reading R14): the largest outlier weight for which the expected
+// number of outliers, with every component density at its peak c_m, does not
+// exceed eta N.  pi_m NULL = uniform 1/M.
+double oracle_w_from_eta(double eta, double V, double sigma2, const double* alpha, const double* pi_m, int64_t M,
+                         int32_t include_alpha_norm) {
+  if (!(eta > 0.0)) return 0.0;
+  if (!(eta < 1.0)) return 1.0;
+  double S = 0.0;
+  const double c0 = std::pow(2.0 * kPi * sigma2, -1.5);
+  for (int64_t m = 0; m < M; ++m) {
+    double pi = pi_m ? pi_m[m] : 1.0 / static_cast<double>(M);
+    double c = c0 * (include_alpha_norm ? std::sqrt(1.0 + alpha[m]) : 1.0);
+    S += pi * c;
+  }
+  const double a = eta * V * S;
+  return a / ((1.0 - eta) + a);
+}
+
 int oracle_register(const float* X, int64_t N, const float* Y, int64_t M, const oracle_params* p,
                     double* R_out, double* t_out, double* sigma2_out, int32_t* iters_out,
                     double* trace, double* normals_out, double* alpha_out) {
-  if (N <= 0 || M <= 0 || p->knn_k <= 0 || p->knn_k > M || !(p->w >= 0.0 && p->w < 1.0))
+  if (N <= 0 || M <= 0 || p->knn_k <= 0 || !(p->w >= 0.0 && p->w < 1.0) || !(p->eta >= 0.0 && p->eta < 1.0))
     return 1;
+  // confidence truncation (Sec. 3.3, reading R15): keep the points with phi >= threshold
+  std::vector<float> Xk, Yk;
+  std::vector<double> phx, phy;
+  std::vector<int64_t> ykeep;
+  for (int64_t n = 0; n < N; ++n) {
+    const double ph = p->phi_x ? p->phi_x[n] : 1.0;
+    if (p->phi_x && p->cf_threshold > 0 && ph < p->cf_threshold) continue;
+    for (int c = 0; c < 3; ++c) Xk.push_back(X[3 * n + c]);
+    phx.push_back(ph);
+  }
+  for (int64_t m = 0; m < M; ++m) {
+    const double ph = p->phi_y ? p->phi_y[m] : 1.0;
+    if (p->phi_y && p->cf_threshold > 0 && ph < p->cf_threshold) continue;
+    for (int c = 0; c < 3; ++c) Yk.push_back(Y[3 * m + c]);
+    phy.push_back(ph);
+    ykeep.push_back(m);
+  }
+  const int64_t M_all = M;
+  N = static_cast<int64_t>(phx.size());
+  M = static_cast<int64_t>(phy.size());
+  X = Xk.data();
+  Y = Yk.data();
+  if (N <= 0 || M <= 0 || p->knn_k > M) return 1;
   int k = p->knn_k;
   std::vector<int32_t> idx(static_cast<size_t>(M * k));
   if (M > 20000)
@@ -864,8 +920,16 @@ int oracle_register(const float* X, int64_t N, const float* Y, int64_t M, const 
       alp(static_cast<size_t>(M));
   oracle_local_geometry(Y, M, idx.data(), k, p->alpha_max, p->lambda, nrm.data(), kap.data(),
                         alp.data());
-  if (normals_out) std::memcpy(normals_out, nrm.data(), sizeof(double) * 3 * M);
-  if (alpha_out) std::memcpy(alpha_out, alp.data(), sizeof(double) * M);
+  // outputs in the caller's target indexing; truncated targets get NaN
+  for (int64_t m = 0; m < M_all && (normals_out || alpha_out); ++m) {
+    if (normals_out) normals_out[3 * m] = normals_out[3 * m + 1] = normals_out[3 * m + 2] = std::nan("");
+    if (alpha_out) alpha_out[m] = std::nan("");
+  }
+  for (int64_t j = 0; j < M; ++j) {
+    if (normals_out)
+      for (int c = 0; c < 3; ++c) normals_out[3 * ykeep[j] + c] = nrm[3 * j + c];
+    if (alpha_out) alpha_out[ykeep[j]] = alp[j];
+  }
   double diag = 0;
   double Vbox = oracle_volume(Y, M, &diag);
   double V = p->volume > 0 ? p->volume : Vbox;
@@ -873,14 +937,30 @@ int oracle_register(const float* X, int64_t N, const float* Y, int64_t M, const 
   double sigma2 = p->sigma2_init > 0 ? p->sigma2_init
                                      : oracle_sigma2_init(X, N, Y, M, p->init_R, p->init_t);
   double floor = p->sigma2_floor_rel * diag * diag;
+  // priors and outlier weights (Secs. 3.2-3.3)
+  std::vector<double> pim, wn;
+  if (p->phi_y) {
+    double sum = 0;
+    for (double v : phy) sum += v;
+    for (double v : phy) pim.push_back(v / sum);
+  }
+  const double w0 = p->eta > 0 ? oracle_w_from_eta(p->eta, V, sigma2, alp.data(), p->phi_y ? pim.data() : nullptr, M,
+                                                   p->include_alpha_norm)
+                               : p->w;
+  if (p->phi_x)
+    for (double v : phx) wn.push_back(1.0 - (1.0 - w0) * v);
+  double nll_prev = 0;
   std::vector<double> stats(static_cast<size_t>(N * kStat));
   std::vector<V3> Xv = to_v3(X, N);
   int it = 0;
   int rc = 0;
   for (; it < p->max_iters; ++it) {
     double nll = 0;
-    oracle_estep(X, N, Y, M, nrm.data(), alp.data(), nullptr, nullptr, p->w, V, g.R.a, &g.t.x,
-                 sigma2, p->include_alpha_norm, p->threads, stats.data(), nullptr, &nll);
+    oracle_estep(X, N, Y, M, nrm.data(), alp.data(), p->phi_y ? pim.data() : nullptr,
+                 p->phi_x ? wn.data() : nullptr, w0, V, g.R.a, &g.t.x, sigma2, p->include_alpha_norm,
+                 p->threads, stats.data(), nullptr, &nll);
+    const bool nll_stop = p->nll_tol > 0 && it > 0 && std::fabs(nll - nll_prev) <= p->nll_tol * std::fabs(nll);
+    nll_prev = nll;
     std::vector<SrcStat> st(static_cast<size_t>(N));
     double NP = 0, Pout = 0;
     for (int64_t n = 0; n < N; ++n) {
@@ -924,7 +1004,7 @@ int oracle_register(const float* X, int64_t N, const float* Y, int64_t M, const 
       tr[6] = nll;
       tr[7] = Pout;
     }
-    if (at_floor || (p->tol > 0 && motion < p->tol)) {
+    if (at_floor || nll_stop || (p->tol > 0 && motion < p->tol)) {
       ++it;
       break;
     }

@@ -380,3 +380,94 @@ def test_permutation_invariance():
     assert oracle.rotation_error(r1["R"], r2["R"]) < 1e-9
     np.testing.assert_allclose(r1["t"], r2["t"], atol=1e-9)
     assert r1["sigma2"] == pytest.approx(r2["sigma2"], rel=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2 (outlier weight from the outlier ratio), Sec. 3.3 (confidence
+# filtering), termination on the log-likelihood of Eq. (4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("alpha_norm", [False, True])
+def test_w_from_eta_makes_the_expected_outlier_count_eta(alpha_norm):
+    """With every component density at its peak c_m, the outlier posterior of
+    each source equals eta exactly at w = w_max (the defining equation)."""
+    rng = np.random.default_rng(21)
+    M = 50
+    alpha = rng.uniform(0, 3, M)
+    pi = rng.uniform(0.5, 2, M)
+    pi /= pi.sum()
+    s2, V = 0.013, 2.7
+    for eta in (0.01, 0.2, 0.6):
+        w = oracle.w_from_eta(eta, V, s2, alpha, pi, include_alpha_norm=alpha_norm)
+        c = (2 * math.pi * s2) ** -1.5 * (np.sqrt(1 + alpha) if alpha_norm else 1.0)
+        S = float((pi * c).sum())
+        A = w / (1 - w) / V
+        assert A / (A + S) == pytest.approx(eta, rel=1e-12)
+    assert oracle.w_from_eta(0.0, V, s2, alpha, pi) == 0.0
+
+
+def test_w_from_eta_closed_form_for_uniform_priors():
+    s2, V, eta = 0.02, 1.3, 0.1
+    c = (2 * math.pi * s2) ** -1.5
+    ref = eta * V * c / ((1 - eta) + eta * V * c)
+    assert oracle.w_from_eta(eta, V, s2, np.zeros(7)) == pytest.approx(ref, rel=1e-13)
+
+
+def test_register_with_eta_uses_w_max_at_the_initial_variance():
+    c = synth.sphere_plane_pair(seed=23, n=200, m=300)
+    X, Y = c["X"], c["Y"]
+    s20 = oracle.sigma2_init(X, Y, np.eye(3), np.zeros(3))
+    V, _ = oracle.volume(Y)
+    w = oracle.w_from_eta(0.15, V, s20, np.zeros(len(Y)))
+    a = oracle.register(X, Y, eta=0.15, max_iters=6)
+    b = oracle.register(X, Y, w=w, max_iters=6)
+    np.testing.assert_array_equal(a["R"], b["R"])
+    np.testing.assert_array_equal(a["t"], b["t"])
+
+
+def test_confidence_special_cases_reduce_to_uniform_weights():
+    """phi = 1 everywhere is the uniform setting; a constant target confidence
+    gives pi = 1/M; a constant source confidence phi0 gives w = 1 - (1 - w0) phi0."""
+    c = synth.sphere_plane_pair(seed=24, n=150, m=250)
+    X, Y = c["X"], c["Y"]
+    base = oracle.register(X, Y, max_iters=5)
+    ones = oracle.register(X, Y, phi_x=np.ones(len(X)), phi_y=np.ones(len(Y)), max_iters=5)
+    np.testing.assert_allclose(ones["R"], base["R"], rtol=0, atol=1e-13)
+    const_y = oracle.register(X, Y, phi_y=np.full(len(Y), 0.37), max_iters=5)
+    np.testing.assert_allclose(const_y["R"], base["R"], rtol=0, atol=1e-13)
+    phi0 = float(np.float32(0.8))  # confidences are FP32 inputs
+    cx = oracle.register(X, Y, phi_x=np.full(len(X), phi0, dtype=np.float32), max_iters=5)
+    ref = oracle.register(X, Y, w=1 - (1 - 0.1) * phi0, max_iters=5)
+    np.testing.assert_allclose(cx["R"], ref["R"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(cx["t"], ref["t"], rtol=0, atol=1e-13)
+
+
+def test_confidence_truncation_is_removal_before_everything():
+    c = synth.sphere_plane_pair(seed=25, n=300, m=400)
+    X, Y = c["X"], c["Y"]
+    rng = np.random.default_rng(25)
+    px = rng.uniform(0.2, 1.0, len(X)).astype(np.float32)
+    py = rng.uniform(0.2, 1.0, len(Y)).astype(np.float32)
+    tau = 0.45
+    a = oracle.register(X, Y, phi_x=px, phi_y=py, cf_threshold=tau, max_iters=5)
+    kx, ky = px >= tau, py >= tau
+    b = oracle.register(X[kx], Y[ky], phi_x=px[kx], phi_y=py[ky], max_iters=5)
+    np.testing.assert_array_equal(a["R"], b["R"])
+    np.testing.assert_array_equal(a["t"], b["t"])
+    assert np.all(np.isnan(a["alpha"][~ky])) and np.all(np.isfinite(a["alpha"][ky]))
+
+
+def test_nll_termination_stops_at_the_first_small_change():
+    c = synth.sphere_plane_pair(seed=26, n=300, m=300)
+    X, Y = c["X"], c["Y"]
+    full = oracle.register(X, Y, max_iters=40)
+    nll = full["trace"][:, 6]
+    change = np.abs(np.diff(nll)) / np.abs(nll[1:])
+    tol = float(np.median(change))
+    rel = change <= tol
+    i = int(np.argmax(rel)) + 1  # first iteration whose E step changed the NLL by <= tol
+    assert rel.any()
+    got = oracle.register(X, Y, max_iters=40, nll_tol=tol)
+    assert got["iters"] == i + 1
+    same = oracle.register(X, Y, max_iters=i + 1)
+    np.testing.assert_array_equal(got["R"], same["R"])
