@@ -385,6 +385,7 @@ def run_batch(args):
         launches += tm["launches"]
     barrier()
     clk = clocks.stop()
+    plan = plan_obj(ctx)
     iters_run = int(got["iters"].max())
     pairs_per_step = float((got["iters"].astype(np.float64) * nm).sum())
 
@@ -446,7 +447,7 @@ def run_batch(args):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4), "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches, "iters_run": iters_run,
-           "e_step_plan": plan_obj(ctx),
+           "e_step_plan": plan,
            "per_pair_form": {"value": pp_pairs / (pp_ms / 1e3), "unit": UNIT, "ms_per_step": round(pp_ms, 3),
                              "calls": P, "batched_speedup": round((pp_ms / pp_pairs) / (ms / pairs_per_step), 3)}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

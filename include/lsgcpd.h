@@ -82,6 +82,26 @@ typedef struct {
   int32_t newton_max; /* inner Newton steps per M step (default 20)                       */
   int32_t precision;  /* 0: FP32 E step (the only mode implemented; others -> EINVAL)     */
   int32_t reserved;
+  /* Outlier weight from the outlier ratio (Sec. 3.2): eta in (0, 1) sets
+   * w0 = w_max = eta V S / ((1 - eta) + eta V S), S = sum_m pi(m) c_m with c_m
+   * the peak of component m, evaluated once at sigma^2_0 (overrides w);
+   * 0 = use w. */
+  double eta;
+  /* Confidence filtering (Sec. 3.3): with phi_y, pi(m) = phi(y_m) / sum phi(y);
+   * with phi_x, w_n = 1 - (1 - w0) phi(x_n).  Points whose phi is below
+   * cf_threshold (> 0) are removed from X and Y before anything else
+   * (neighbourhoods, sigma^2_0, V and the priors are those of the kept points).
+   * phi_x / phi_y: N / M floats in (0, 1], in the same memory (host or device)
+   * and with the same offsets as X / Y, or NULL (phi = 1).  Registration calls
+   * only (lsgcpd_register, lsgcpd_register_batch) and lsgcpd_estep (no
+   * truncation there). */
+  double cf_threshold;
+  /* Termination on the log-likelihood (Eq. (4)): > 0 stops EM after the M step
+   * of the first iteration i >= 1 whose E step changed the NLL by at most
+   * nll_tol |NLL_i|; 0 = off. */
+  double nll_tol;
+  const float* phi_x;
+  const float* phi_y;
 } lsgcpd_params;
 
 /* Result of a registration (host struct filled by lsgcpd_register). */
@@ -150,7 +170,10 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* ctx, const float* Y, int64_t M, cons
  *           [0] Pbar = sum_m P_mn, [1..3] h = sum_m P_mn Lambda_m r_mn,
  *           [4..9] W = sum_m P_mn alpha_m n_m n_m^T (00,01,02,11,12,22),
  *           [10] D = sum_m P_mn d_mn, d = r^T Lambda_m r, [11] Pout, [12..15] 0.
- * Uses p->w (0 allowed: no outlier term) and p->include_alpha_norm. */
+ * Uses p->w (0 allowed: no outlier term) as w0, p->include_alpha_norm and the
+ * optional confidences p->phi_x / p->phi_y (DEVICE arrays of N / M floats;
+ * Sec. 3.3: pi(m) = phi_m / sum phi, w_n = 1 - (1 - w0) phi_n; no truncation
+ * and no eta here). */
 lsgcpd_status lsgcpd_estep(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y,
                            const float* normals, const float* alpha, int64_t M,
                            const lsgcpd_params* p, const double R[9], const double t[3],
@@ -253,7 +276,9 @@ lsgcpd_status lsgcpd_register_batch(lsgcpd_ctx* ctx, int32_t num_pairs, const fl
  * stream capture.  Every call shares the one arena and leaves its contents
  * behind: concurrent or overlapping calls (other threads, other streams whose
  * work has not finished) race on it and must be serialised by the caller.
- * The call synchronises `stream` before returning. */
+ * The call synchronises `stream` before returning.  The confidence fields of
+ * the parameter block (phi_x, phi_y, cf_threshold) and eta are not used here:
+ * uniform priors and outlier weight w. */
 lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const float* Y, const float* normals,
                                    const float* alpha, int64_t M, const lsgcpd_params* p,
                                    const double R[9], const double t[3], double sigma2, double volume,

@@ -36,6 +36,8 @@ class Params(C.Structure):
         ("init_t", C.c_double * 3), ("newton_tol", C.c_double), ("sigma2_floor_rel", C.c_double),
         ("knn_k", C.c_int32), ("max_iters", C.c_int32), ("include_alpha_norm", C.c_int32),
         ("newton_max", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("eta", C.c_double), ("cf_threshold", C.c_double), ("nll_tol", C.c_double),
+        ("phi_x", C.c_void_p), ("phi_y", C.c_void_p),
     ]
 
 
@@ -140,6 +142,43 @@ def _any_ptr(a, name):
     return C.c_void_p(arr.ctypes.data), arr.shape[0], arr
 
 
+def _vec_ptr(a, name, n):
+    """Pointer to a float32 vector of n values on host (numpy / CPU tensor) or device (CUDA tensor)."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous() or a.numel() != n:
+                raise ValueError(f"{name} must be a contiguous float32 tensor of {n} values")
+            return a.data_ptr(), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32).ravel())
+    if arr.size != n:
+        raise ValueError(f"{name} must have {n} values")
+    return arr.ctypes.data, arr
+
+
+class _Confidences:
+    """Sets params.phi_x / phi_y for the duration of one call (and keeps the arrays alive)."""
+
+    def __init__(self, params, phi_x, n, phi_y, m):
+        self.params = params
+        self.px, self.kx = _vec_ptr(phi_x, "phi_x", n)
+        self.py, self.ky = _vec_ptr(phi_y, "phi_y", m)
+
+    def __enter__(self):
+        self.old = (self.params.phi_x, self.params.phi_y)
+        self.params.phi_x = self.px
+        self.params.phi_y = self.py
+        return self.params
+
+    def __exit__(self, *exc):
+        self.params.phi_x, self.params.phi_y = self.old
+        return False
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -189,9 +228,16 @@ def lsgcpd_preprocess(ctx, Y, params, want_idx=False, stream=None):
     return dict(normals=normals, kappa=kappa, alpha=alpha, idx=idx)
 
 
-def lsgcpd_estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None):
+def lsgcpd_estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None, phi_x=None,
+                 phi_y=None):
     import torch
     N, M = X.shape[0], Y.shape[0]
+    with _Confidences(params, phi_x, N, phi_y, M) as params:
+        return _estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n, stream, N, M)
+
+
+def _estep(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n, stream, N, M):
+    import torch
     _dev_ptr(X, "X", (N, 3))
     _dev_ptr(Y, "Y", (M, 3))
     _dev_ptr(normals, "normals", (M, 3))
@@ -249,14 +295,16 @@ def lsgcpd_mstep(ctx, moments, R, t, params, stream=None):
                 halvings=info[2])
 
 
-def lsgcpd_register(ctx, X, Y, params, trace=False, stream=None):
+def lsgcpd_register(ctx, X, Y, params, trace=False, stream=None, phi_x=None, phi_y=None):
+    """phi_x / phi_y: optional confidences (Sec. 3.3), in the same memory (host / device) as X / Y."""
     xp, N, _xk = _any_ptr(X, "X")
     yp, M, _yk = _any_ptr(Y, "Y")
     res = Result()
     tr = np.zeros((max(params.max_iters, 1), TRACE_WIDTH)) if trace else None
-    rc = lib().lsgcpd_register(ctx, xp, N, yp, M, C.byref(params), C.byref(res),
-                               tr.ctypes.data_as(C.POINTER(C.c_double)) if tr is not None else None,
-                               _stream(stream))
+    with _Confidences(params, phi_x, N, phi_y, M) as pp:
+        rc = lib().lsgcpd_register(ctx, xp, N, yp, M, C.byref(pp), C.byref(res),
+                                   tr.ctypes.data_as(C.POINTER(C.c_double)) if tr is not None else None,
+                                   _stream(stream))
     _check(ctx, rc)
     out = dict(R=np.array(res.R[:]).reshape(3, 3), t=np.array(res.t[:]), sigma2=res.sigma2,
                iters=res.iters, mode=res.mode, ms_estep=res.ms_estep, ms_total=res.ms_total)
@@ -265,8 +313,9 @@ def lsgcpd_register(ctx, X, Y, params, trace=False, stream=None):
     return out
 
 
-def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=None):
-    """Register every pair i: X[n_off[i]:n_off[i+1]] onto Y[m_off[i]:m_off[i+1]]."""
+def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=None, phi_x=None, phi_y=None):
+    """Register every pair i: X[n_off[i]:n_off[i+1]] onto Y[m_off[i]:m_off[i+1]].
+    phi_x / phi_y: optional confidences with the same offsets and memory as X / Y."""
     xp, _N, _xk = _any_ptr(X, "X")
     yp, _M, _yk = _any_ptr(Y, "Y")
     no = np.ascontiguousarray(np.asarray(n_off, dtype=np.int64))
@@ -282,10 +331,11 @@ def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=N
     it = np.zeros(P, dtype=np.int32)
     tr = np.zeros((P, max(params.max_iters, 1), TRACE_WIDTH)) if trace else None
     dptr = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
-    rc = lib().lsgcpd_register_batch(ctx, P, xp, no.ctypes.data_as(C.POINTER(C.c_int64)), yp,
-                                     mo.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(params), dptr(R),
-                                     dptr(t), dptr(s2), it.ctypes.data_as(C.POINTER(C.c_int32)),
-                                     dptr(tr) if tr is not None else None, _stream(stream))
+    with _Confidences(params, phi_x, int(_N), phi_y, int(_M)) as pp:
+        rc = lib().lsgcpd_register_batch(ctx, P, xp, no.ctypes.data_as(C.POINTER(C.c_int64)), yp,
+                                         mo.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(pp), dptr(R),
+                                         dptr(t), dptr(s2), it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                         dptr(tr) if tr is not None else None, _stream(stream))
     _check(ctx, rc)
     out = dict(R=R, t=t, sigma2=s2, iters=it)
     if tr is not None:
@@ -337,17 +387,19 @@ class Context:
     def preprocess(self, Y, params, want_idx=False, stream=None):
         return lsgcpd_preprocess(self.handle, Y, params, want_idx, stream)
 
-    def estep(self, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None):
-        return lsgcpd_estep(self.handle, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n, stream)
+    def estep(self, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n=False, stream=None, phi_x=None,
+              phi_y=None):
+        return lsgcpd_estep(self.handle, X, Y, normals, alpha, R, t, sigma2, volume, params, per_n, stream,
+                            phi_x, phi_y)
 
     def mstep(self, moments, R, t, params, stream=None):
         return lsgcpd_mstep(self.handle, moments, R, t, params, stream)
 
-    def register(self, X, Y, params, trace=False, stream=None):
-        return lsgcpd_register(self.handle, X, Y, params, trace, stream)
+    def register(self, X, Y, params, trace=False, stream=None, phi_x=None, phi_y=None):
+        return lsgcpd_register(self.handle, X, Y, params, trace, stream, phi_x, phi_y)
 
-    def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None):
-        return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream)
+    def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None, phi_x=None, phi_y=None):
+        return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream, phi_x, phi_y)
 
     def set_autotune(self, enable):
         lsgcpd_set_autotune(self.handle, enable)

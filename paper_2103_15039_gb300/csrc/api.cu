@@ -48,6 +48,9 @@ struct lsgcpd_ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevBuf<float> X_in, Y_in, rec, part, knn_d, ls_n, gam_n;
+  DevBuf<float> phx_in, phy_in, Xc, Yc, phxc, phyc;  // confidences; truncated clouds
+  DevBuf<int> cnt, coff;
+  DevBuf<long long> toff;
   DevBuf<float4> xs, y4, yl;
   DevBuf<int> knn_i, knn_idx, tab;
   DevBuf<long long> off64;
@@ -130,6 +133,10 @@ lsgcpd_status check_params(lsgcpd_ctx* c, const lsgcpd_params* p) {
   if (p->max_iters < 0 || p->max_iters > 100000) return fail(c, LSGCPD_EINVAL, "max_iters out of range");
   if (p->newton_max < 1 || p->newton_max > 1000) return fail(c, LSGCPD_EINVAL, "newton_max out of range");
   if (p->precision != 0) return fail(c, LSGCPD_EINVAL, "only precision 0 (FP32 E step) is implemented");
+  if (!(p->eta >= 0.0 && p->eta < 1.0)) return fail(c, LSGCPD_EINVAL, "eta must be in [0, 1)");
+  if (!is_finite_d(p->cf_threshold) || p->cf_threshold < 0.0)
+    return fail(c, LSGCPD_EINVAL, "cf_threshold must be finite and >= 0");
+  if (!is_finite_d(p->nll_tol) || p->nll_tol < 0.0) return fail(c, LSGCPD_EINVAL, "nll_tol must be finite and >= 0");
   return LSGCPD_OK;
 }
 
@@ -146,6 +153,9 @@ DevParams dev_params(const lsgcpd_params* p) {
   d.newton_max = p->newton_max;
   d.include_alpha_norm = p->include_alpha_norm;
   d.max_iters = p->max_iters;
+  d.cf_x = p->phi_x ? 1 : 0;
+  d.eta = p->eta;
+  d.nll_tol = p->nll_tol;
   return d;
 }
 
@@ -174,6 +184,23 @@ __global__ void check_finite_kernel(const float* p, long long n, int* status) {
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
     bad |= !isfinite(p[i]);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 8);
+}
+
+// Confidences must lie in (0, 1] (NaN fails too): status bit 16.
+__global__ void check_conf_kernel(const float* p, long long n, int* status) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  bool bad = false;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    bad |= !(p[i] > 0.f && p[i] <= 1.f);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 16);
+}
+
+cudaError_t check_conf(const float* p, long long n, int* status, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 1024) b = 1024;
+  if (b < 1) b = 1;
+  check_conf_kernel<<<static_cast<unsigned>(b), 256, 0, s>>>(p, n, status);
+  return cudaGetLastError();
 }
 
 cudaError_t check_finite(const float* p, long long n, int* status, cudaStream_t s) {
@@ -225,7 +252,7 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
   grow(c->off64, p.off64.size());
   grow(c->st, static_cast<size_t>(g.P));
   grow(c->mom, static_cast<size_t>(g.P) * kGlob);
-  grow(c->red, static_cast<size_t>(g.P) * chunks * 20);
+  grow(c->red, static_cast<size_t>(g.P) * chunks * 24);
   grow(c->trace, static_cast<size_t>(g.P) * (iters > 0 ? iters : 1) * LSGCPD_TRACE_WIDTH);
   if (k > 0) {
     const int splits = knn_splits(g, c->num_sms);
@@ -252,13 +279,13 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
 
 Dev dev_of(lsgcpd_ctx* c) { return Dev{c->tab.p, c->off64.p, c->st.p, c->done_count}; }
 
-// The plan's tables, and the words that must start at zero, for this call.
+// The plan's tables and the finished-pair count (zero) for this call.  The
+// status word is cleared separately, before the input checks that set it.
 cudaError_t upload_plan(lsgcpd_ctx* c, const BatchPlan& p, cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(c->tab.p, p.tab.data(), sizeof(int) * p.tab.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->off64.p, p.off64.data(), sizeof(long long) * p.off64.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->done_count, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
   return e;
 }
 
@@ -317,17 +344,161 @@ void moments_to_raw(const double* mc, const double mu[3], double* mr) {
 
 // One or more registrations: X and Y are the concatenated clouds (host or
 // device), sizes N[i], M[i].  Results per pair in the caller's frame.
-lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N,
-                               const std::vector<long long>& M, const lsgcpd_params* p, double* R_out, double* t_out,
-                               double* sigma2_out, int32_t* iters_out, int32_t* mode_out, double* trace,
-                               void* stream) {
-  const int P = static_cast<int>(N.size());
+// Inputs of a registration on the device: host arrays copied in, confidences
+// checked, and (Sec. 3.3) the points below the confidence threshold removed.
+struct Staged {
+  const float* X = nullptr;
+  const float* Y = nullptr;
+  const float* phx = nullptr;
+  const float* phy = nullptr;
+  std::vector<long long> N, M;
+  int64_t h2d = 0;
+  int64_t launches = 0;
+};
+
+// Stable per-pair removal of the rows whose confidence is below the threshold
+// (one host round trip for the kept counts).
+lsgcpd_status compact_side(lsgcpd_ctx* c, const float* rows, const float* phi, std::vector<long long>& sizes,
+                           float thr, DevBuf<float>& rows_out, DevBuf<float>& phi_out, int64_t* launches) {
+  cudaStream_t s = c->stream;
+  const int P = static_cast<int>(sizes.size());
+  long long big = 1;
+  std::vector<long long> off(P + 1, 0);
+  for (int i = 0; i < P; ++i) {
+    off[i + 1] = off[i] + sizes[i];
+    big = std::max(big, sizes[i]);
+  }
+  const int chunks = compact_chunks(big);
+  LSG_CUDA(ensure(c->cnt, static_cast<size_t>(P) * chunks), "alloc");
+  LSG_CUDA(ensure(c->coff, static_cast<size_t>(P) * chunks), "alloc");
+  LSG_CUDA(ensure(c->toff, 2 * static_cast<size_t>(P + 1)), "alloc");
+  LSG_CUDA(cudaMemcpyAsync(c->toff.p, off.data(), sizeof(long long) * (P + 1), cudaMemcpyHostToDevice, s), "copy");
+  LSG_CUDA(launch_compact_count(phi, c->toff.p, P, chunks, thr, c->cnt.p, s), "compact");
+  std::vector<int> cnt(static_cast<size_t>(P) * chunks);
+  int status = 0;
+  LSG_CUDA(cudaMemcpyAsync(cnt.data(), c->cnt.p, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaStreamSynchronize(s), "sync");
+  if (status & 8) return fail(c, LSGCPD_EINVAL, "inputs contain NaN or Inf");
+  if (status & 16) return fail(c, LSGCPD_EINVAL, "confidences must lie in (0, 1]");
+  std::vector<int> coff(cnt.size());
+  std::vector<long long> out_off(P + 1, 0);
+  for (int i = 0; i < P; ++i) {
+    long long run = 0;
+    for (int j = 0; j < chunks; ++j) {
+      coff[static_cast<size_t>(i) * chunks + j] = static_cast<int>(run);
+      run += cnt[static_cast<size_t>(i) * chunks + j];
+    }
+    sizes[i] = run;
+    out_off[i + 1] = out_off[i] + run;
+  }
+  LSG_CUDA(ensure(rows_out, static_cast<size_t>(out_off[P]) * 3), "alloc");
+  LSG_CUDA(ensure(phi_out, static_cast<size_t>(out_off[P])), "alloc");
+  LSG_CUDA(cudaMemcpyAsync(c->coff.p, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice, s), "copy");
+  LSG_CUDA(cudaMemcpyAsync(c->toff.p + (P + 1), out_off.data(), sizeof(long long) * (P + 1), cudaMemcpyHostToDevice,
+                           s),
+           "copy");
+  LSG_CUDA(launch_compact_scatter(rows, phi, c->toff.p, c->toff.p + (P + 1), c->coff.p, P, chunks, thr, rows_out.p,
+                                  phi_out.p, s),
+           "compact");
+  *launches += 2;
+  // the host vectors above are staged by the copies before these calls return
+  return LSGCPD_OK;
+}
+
+lsgcpd_status stage(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N,
+                    const std::vector<long long>& M, const lsgcpd_params* p, bool xd, bool yd, Staged* in) {
+  cudaStream_t s = c->stream;
+  long long Ntot = 0, Mtot = 0;
+  for (long long v : N) Ntot += v;
+  for (long long v : M) Mtot += v;
+  in->N = N;
+  in->M = M;
+  in->X = X;
+  in->Y = Y;
+  in->phx = p->phi_x;
+  in->phy = p->phi_y;
+  auto up = [&](DevBuf<float>& buf, const float* h, long long n) -> cudaError_t {
+    cudaError_t e = ensure(buf, static_cast<size_t>(n));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf.p, h, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    in->h2d += 4 * n;
+    return e;
+  };
+  if (!xd) {
+    LSG_CUDA(up(c->X_in, X, 3 * Ntot), "copy X");
+    in->X = c->X_in.p;
+  }
+  if (!yd) {
+    LSG_CUDA(up(c->Y_in, Y, 3 * Mtot), "copy Y");
+    in->Y = c->Y_in.p;
+  }
+  if (p->phi_x && !xd) {
+    LSG_CUDA(up(c->phx_in, p->phi_x, Ntot), "copy phi_x");
+    in->phx = c->phx_in.p;
+  }
+  if (p->phi_y && !yd) {
+    LSG_CUDA(up(c->phy_in, p->phi_y, Mtot), "copy phi_y");
+    in->phy = c->phy_in.p;
+  }
+  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
+  LSG_CUDA(check_finite(in->X, Ntot * 3, c->status, s), "check");
+  LSG_CUDA(check_finite(in->Y, Mtot * 3, c->status, s), "check");
+  in->launches += 2;
+  if (in->phx) {
+    LSG_CUDA(check_conf(in->phx, Ntot, c->status, s), "check");
+    ++in->launches;
+  }
+  if (in->phy) {
+    LSG_CUDA(check_conf(in->phy, Mtot, c->status, s), "check");
+    ++in->launches;
+  }
+  const float thr = static_cast<float>(p->cf_threshold);
+  if (p->cf_threshold > 0.0 && in->phx) {
+    lsgcpd_status r = compact_side(c, in->X, in->phx, in->N, thr, c->Xc, c->phxc, &in->launches);
+    if (r != LSGCPD_OK) return r;
+    in->X = c->Xc.p;
+    in->phx = c->phxc.p;
+  }
+  if (p->cf_threshold > 0.0 && in->phy) {
+    lsgcpd_status r = compact_side(c, in->Y, in->phy, in->M, thr, c->Yc, c->phyc, &in->launches);
+    if (r != LSGCPD_OK) return r;
+    in->Y = c->Yc.p;
+    in->phy = c->phyc.p;
+  }
+  for (size_t i = 0; i < in->N.size(); ++i) {
+    if (in->N[i] < 1 || in->M[i] < 1)
+      return fail(c, LSGCPD_EINVAL, "confidence truncation left a pair without points");
+    if (p->knn_k > in->M[i]) return fail(c, LSGCPD_EINVAL, "knn_k must not exceed the target count of any pair");
+  }
+  return LSGCPD_OK;
+}
+
+// One or more registrations: X and Y are the concatenated clouds (host or
+// device), sizes N[i], M[i].  Results per pair in the caller's frame.
+lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N_in,
+                               const std::vector<long long>& M_in, const lsgcpd_params* p, double* R_out,
+                               double* t_out, double* sigma2_out, int32_t* iters_out, int32_t* mode_out,
+                               double* trace, void* stream) {
+  const int P = static_cast<int>(N_in.size());
   const int k = p->knn_k;
-  for (int i = 0; i < P; ++i)
-    if (k > M[i]) return fail(c, LSGCPD_EINVAL, "knn_k must not exceed the target count of any pair");
   LSG_CUDA(enter(c, stream), "stream");
+  cudaStream_t s = c->stream;
   const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
   const int iters = p->max_iters;
+  if (c->timing) {
+    LSG_CUDA(ensure_iter_events(c, iters > 0 ? iters : 1), "events");
+    LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
+  }
+  Staged in;
+  lsgcpd_status rs = stage(c, X, Y, N_in, M_in, p, xd, yd, &in);
+  if (rs != LSGCPD_OK) {
+    leave(c, stream);
+    return rs;
+  }
+  const std::vector<long long>& N = in.N;
+  const std::vector<long long>& M = in.M;
+  const float* Xd = in.X;
+  const float* Yd = in.Y;
   // source tile: measured once per problem shape (cached), else the plan's heuristic
   std::vector<long long> skey = N;
   skey.insert(skey.end(), M.begin(), M.end());
@@ -342,53 +513,47 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   std::vector<BatchPlan> cands;
   if (tune)
     for (int S : {4, 2, 1}) cands.push_back(S == plan.g.S ? plan : plan_batch(N, M, c->num_sms, S));
-  const long long Ntot = plan.off64[P], Mtot = plan.off64[2 * P + 1];
-  lsgcpd_status rs = reserve(c, plan, k, iters, !xd || !yd);
-  for (size_t i = 0; i < cands.size() && rs == LSGCPD_OK; ++i) rs = reserve(c, cands[i], k, iters, !xd || !yd);
+  rs = reserve(c, plan, k, iters, false);
+  for (size_t i = 0; i < cands.size() && rs == LSGCPD_OK; ++i) rs = reserve(c, cands[i], k, iters, false);
   if (rs != LSGCPD_OK) return rs;
-  cudaStream_t s = c->stream;
   const Dev d = dev_of(c);
-  if (c->timing) {
-    LSG_CUDA(ensure_iter_events(c, iters > 0 ? iters : 1), "events");
-    LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
-  }
-  const float* Xd = X;
-  const float* Yd = Y;
-  if (!xd) {
-    LSG_CUDA(cudaMemcpyAsync(c->X_in.p, X, sizeof(float) * 3 * Ntot, cudaMemcpyHostToDevice, s), "copy X");
-    Xd = c->X_in.p;
-  }
-  if (!yd) {
-    LSG_CUDA(cudaMemcpyAsync(c->Y_in.p, Y, sizeof(float) * 3 * Mtot, cudaMemcpyHostToDevice, s), "copy Y");
-    Yd = c->Y_in.p;
-  }
-  LSG_CUDA(upload_plan(c, plan, s), "plan");
-  int64_t launches = 0;
-  LSG_CUDA(check_finite(Xd, Ntot * 3, c->status, s), "check");
-  LSG_CUDA(check_finite(Yd, Mtot * 3, c->status, s), "check");
+  int64_t launches = in.launches;
   const DevParams dp = dev_params(p);
-  LSG_CUDA(launch_init(plan, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
+  // the EM state of every pair: centring, V, sigma^2_0, then w0 from the outlier ratio if asked
+  auto init_state = [&](const BatchPlan& pl) -> cudaError_t {
+    cudaError_t e = launch_init(pl, d, Xd, Yd, in.phx, in.phy, dp, true, c->red.p, c->xs.p, s);
+    if (e == cudaSuccess && p->eta > 0.0) e = launch_eta(pl, d, c->yl.p, p->eta, s);
+    launches += 4 + (p->eta > 0.0 ? 1 : 0);
+    return e;
+  };
+  LSG_CUDA(upload_plan(c, plan, s), "plan");
+  LSG_CUDA(launch_init(plan, d, Xd, Yd, in.phx, in.phy, dp, true, c->red.p, c->xs.p, s), "init");
   const int splits = knn_splits(plan.g, c->num_sms);
   LSG_CUDA(launch_knn(plan, d, Yd, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, s), "knn");
-  LSG_CUDA(launch_geometry(plan, d, Yd, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
-                           c->yl.p, nullptr, nullptr, nullptr, s),
+  LSG_CUDA(launch_geometry(plan, d, Yd, in.phy, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm,
+                           c->rec.p, c->yl.p, nullptr, nullptr, nullptr, s),
            "geometry");
-  launches += 2 + 4 + 3 + 1;
+  launches += 4 + 3 + 1;
+  if (p->eta > 0.0) {
+    LSG_CUDA(launch_eta(plan, d, c->yl.p, p->eta, s), "eta");
+    ++launches;
+  }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
   std::vector<EmState> hs(P);
   int status = 0;
   LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");
   LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
-  if (status & 8) {
+  if (status & (8 | 16)) {
     leave(c, stream);
-    return fail(c, LSGCPD_EINVAL, "inputs contain NaN or Inf");
+    return fail(c, LSGCPD_EINVAL, (status & 8) ? "inputs contain NaN or Inf" : "confidences must lie in (0, 1]");
   }
-  // one shift mode for the whole batch: fixed shift only if it is safe for every pair
+  // one shift mode for the whole batch: fixed shift only if it is safe for every pair, l_m is
+  // uniform (the uniform-shift moments assume one l) and w_n is uniform
   const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
-  // per-source shifts also when l_m varies (the uniform-shift moments assume one l)
-  int mode = p->include_alpha_norm ? 1 : 0;
-  for (int i = 0; i < P; ++i) mode |= choose_mode(p->w, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
+  int mode = (p->include_alpha_norm || in.phx || in.phy) ? 1 : 0;
+  for (int i = 0; i < P; ++i) mode |= choose_mode(hs[i].w0, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
+  const int cfx = in.phx ? 1 : 0;
   if (tune) {
     // time one E-step launch (after a warm-up launch) for every source tile and keep the fastest;
     // the target records do not depend on it, the source layout and the EM state are rebuilt
@@ -396,9 +561,9 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     double best = 1e300;
     for (const BatchPlan& pc : cands) {
       LSG_CUDA(upload_plan(c, pc, s), "plan");
-      LSG_CUDA(launch_init(pc, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
+      LSG_CUDA(init_state(pc), "init");
       LSG_CUDA(launch_prescale(pc, d, c->yl.p, mode, c->rec.p, s), "prescale");
-      if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s), "shift");
+      if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s), "shift");
       LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[0], s), "event");
       LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
@@ -410,15 +575,14 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         best = ms;
         rec.S = pc.g.S;
       }
-      launches += (mode ? 6 : 5) + 2;
+      launches += (mode ? 4 : 3);
     }
     for (const BatchPlan& pc : cands)
       if (pc.g.S == rec.S) plan = pc;
     c->tuned.push_back(rec);
     hit = &c->tuned.back();
     LSG_CUDA(upload_plan(c, plan, s), "plan");
-    LSG_CUDA(launch_init(plan, d, Xd, Yd, dp, true, c->red.p, c->xs.p, s), "init");
-    launches += 4;
+    LSG_CUDA(init_state(plan), "init");
   }
   const Geo& g = plan.g;
   c->last_plan[0] = g.S;
@@ -448,12 +612,14 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
         if (ce == cudaSuccess) ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
-        if (ce == cudaSuccess && mode == 1) ce = launch_shift(plan, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s);
+        if (ce == cudaSuccess && mode == 1)
+          ce = launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s);
         if (ce == cudaSuccess) ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
-          ce = launch_combine(plan, d, c->xs.p, c->part.p, mode, c->ls_n.p, c->gam_n.p, c->rows.p, nullptr, s);
+          ce = launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, nullptr,
+                              s);
         if (ce == cudaSuccess) ce = launch_final_reduce(plan, d, c->rows.p, c->mom.p, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
@@ -487,7 +653,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
   LSG_CUDA(leave(c, stream), "stream");
   c->launches = launches;
-  c->h2d_bytes = (xd ? 0 : 12 * Ntot) + (yd ? 0 : 12 * Mtot) +
+  c->h2d_bytes = in.h2d +
                  static_cast<int64_t>(sizeof(int) * plan.tab.size() + sizeof(long long) * plan.off64.size());
   c->d2h_bytes = 2 * static_cast<int64_t>(sizeof(EmState) * P + sizeof(int)) +
                  (trace && iters > 0 ? static_cast<int64_t>(sizeof(double)) * LSGCPD_TRACE_WIDTH * iters * P : 0);
@@ -589,6 +755,9 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  void* bufs2[] = {c->phx_in.p, c->phy_in.p, c->Xc.p, c->Yc.p, c->phxc.p, c->phyc.p, c->cnt.p, c->coff.p, c->toff.p};
+  for (void* q : bufs2)
+    if (q) cudaFree(q);
   void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->ls_n.p, c->gam_n.p,
                   c->xs.p,   c->y4.p,  c->yl.p,      c->knn_i.p, c->knn_idx.p, c->tab.p, c->off64.p, c->rows.p,
                   c->red.p,  c->trace.p,   c->io.p,  c->mom.p,   c->st.p,    c->status,  c->done_count};
@@ -654,13 +823,15 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   cudaStream_t s = c->stream;
   const Dev d = dev_of(c);
   LSG_CUDA(upload_plan(c, plan, s), "plan");
+  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
   LSG_CUDA(check_finite(Y, M * 3, c->status, s), "check");
   const DevParams dp = dev_params(p);
-  LSG_CUDA(launch_init(plan, d, Y, Y, dp, false, c->red.p, c->xs.p, s), "center");
+  LSG_CUDA(launch_init(plan, d, Y, Y, nullptr, nullptr, dp, false, c->red.p, c->xs.p, s), "center");
   const int splits = knn_splits(plan.g, c->num_sms);
   int* idx = knn_idx ? knn_idx : c->knn_idx.p;
   LSG_CUDA(launch_knn(plan, d, Y, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, idx, s), "knn");
-  LSG_CUDA(launch_geometry(plan, d, Y, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p, c->yl.p,
+  LSG_CUDA(launch_geometry(plan, d, Y, nullptr, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
+                           c->yl.p,
                            normals, kappa, alpha, s),
            "geometry");
   c->launches = 7;
@@ -694,25 +865,36 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   cudaStream_t s = c->stream;
   const Dev d = dev_of(c);
   LSG_CUDA(upload_plan(c, plan, s), "plan");
+  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
   LSG_CUDA(check_finite(X, N * 3, c->status, s), "check");
   LSG_CUDA(check_finite(Y, M * 3, c->status, s), "check");
   LSG_CUDA(check_finite(normals, M * 3, c->status, s), "check");
   LSG_CUDA(check_finite(alpha, M, c->status, s), "check");
-  const DevParams dp = dev_params(p);
-  LSG_CUDA(launch_init(plan, d, X, Y, dp, false, c->red.p, c->xs.p, s), "center");
-  LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
-  LSG_CUDA(launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c->rec.p, c->yl.p, s), "pack");
-  const int mode = p->include_alpha_norm ? 1 : choose_mode(p->w, sigma2, volume, M, 0.0);
   int64_t launches = 10;
+  if (p->phi_x) {
+    LSG_CUDA(check_conf(p->phi_x, N, c->status, s), "check");
+    ++launches;
+  }
+  if (p->phi_y) {
+    LSG_CUDA(check_conf(p->phi_y, M, c->status, s), "check");
+    ++launches;
+  }
+  const DevParams dp = dev_params(p);
+  LSG_CUDA(launch_init(plan, d, X, Y, p->phi_x, p->phi_y, dp, false, c->red.p, c->xs.p, s), "center");
+  LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
+  LSG_CUDA(launch_pack(plan, d, Y, p->phi_y, normals, alpha, p->include_alpha_norm, c->rec.p, c->yl.p, s), "pack");
+  const int cfx = p->phi_x ? 1 : 0;
+  const int mode =
+      (p->include_alpha_norm || p->phi_x || p->phi_y) ? 1 : choose_mode(p->w, sigma2, volume, M, 0.0);
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   LSG_CUDA(launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s), "prescale");
   if (mode == 1) {
-    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, c->ls_n.p, c->gam_n.p, s), "shift");
+    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s), "shift");
     ++launches;
   }
   LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, c->ls_n.p, c->gam_n.p, c->rows.p, per_n, s),
+  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, per_n, s),
            "combine");
   LSG_CUDA(launch_final_reduce(plan, d, c->rows.p, c->mom.p, s), "reduce");
   launches += 3;
@@ -736,6 +918,7 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
     c->last_timing[4] = 0;
   }
   if (status & 8) return fail(c, LSGCPD_EINVAL, "inputs contain NaN or Inf");
+  if (status & 16) return fail(c, LSGCPD_EINVAL, "confidences must lie in (0, 1]");
   if (status & kStatusTimeout) return fail(c, LSGCPD_ETIMEOUT, "E-step tile wait timed out");
   if (moments) moments_to_raw(mom, hs.mu_x, moments);
   return LSGCPD_OK;

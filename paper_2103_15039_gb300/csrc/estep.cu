@@ -339,8 +339,8 @@ constexpr int kShiftThreads = 128;
 
 __global__ void __launch_bounds__(kShiftThreads)
     shift_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
-                 const int* __restrict__ tab, const long long* __restrict__ off64,
-                 const int* __restrict__ done_count, float* __restrict__ ls_n, float* __restrict__ gam_n, Geo g) {
+                 const int* __restrict__ tab, const int* __restrict__ done_count, int cf_x,
+                 float* __restrict__ ls_n, float* __restrict__ gam_n, Geo g) {
   __shared__ __align__(16) float tile[7 * kTile];
   if (*done_count >= g.P) return;
   // every CTA covers kShiftThreads sources of one source block (SB is a multiple)
@@ -372,7 +372,12 @@ __global__ void __launch_bounds__(kShiftThreads)
     }
   }
   // padding sources (zero x) get finite values too; they are never read back
-  const float Lg = sp->L;  // log2 gamma (-inf without outlier term)
+  // log2 gamma_n (-inf without outlier term); per source with confidences: w_n = 1 - (1 - w0) phi_n
+  float Lg = sp->L;
+  if (cf_x) {
+    const float wn = 1.f - static_cast<float>(1.0 - sp->w0) * x.w;
+    Lg = (wn > 0.f ? log2f(wn) - log2f(1.f - wn) : -INFINITY) + sp->Lb;
+  }
   const float L = fmaxf(-best, Lg);
   ls_n[n] = L;
   gam_n[n] = exp2f(Lg - L);  // gamma'_n = 2^(log2 gamma - L_n)
@@ -396,7 +401,7 @@ constexpr int kCPad = kGlob + 1;  // odd row pitch: conflict-free transposition
 __global__ void __launch_bounds__(kCombineThreads)
     combine_kernel(const float4* __restrict__ xs, const float* __restrict__ part, const int* __restrict__ tab,
                    const long long* __restrict__ off64, const EmState* __restrict__ st,
-                   const int* __restrict__ done_count, int mode, const float* __restrict__ ls_n,
+                   const int* __restrict__ done_count, int mode, int cf_x, const float* __restrict__ ls_n,
                    const float* __restrict__ gam_n, double* __restrict__ rows, float* __restrict__ per_n, Geo g) {
   __shared__ float buf[kCombineWarps][32 * kCPad];
   __shared__ double acc[kCombineWarps][kGlob];
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(kCombineThreads)
   float m[kMom], cmp[kMom];
 #pragma unroll
   for (int k = 0; k < kMom; ++k) m[k] = cmp[k] = 0.f;
-  float x0 = 0.f, x1 = 0.f, x2 = 0.f, gp = 0.f, L = 0.f, lam = 0.f;
+  float x0 = 0.f, x1 = 0.f, x2 = 0.f, xw = 1.f, gp = 0.f, L = 0.f, lam = 0.f;
   if (valid) {
     const int first = tab[g.o_block_slot + 2 * b];
     const int count = tab[g.o_block_slot + 2 * b + 1];
@@ -437,6 +442,7 @@ __global__ void __launch_bounds__(kCombineThreads)
     x0 = x.x;
     x1 = x.y;
     x2 = x.z;
+    xw = x.w;
     if (mode) {
       L = ls_n[n];
       gp = gam_n[n];
@@ -466,7 +472,12 @@ __global__ void __launch_bounds__(kCombineThreads)
               W22 = m[9] * inv;
   const float Dn = D * inv;
   const float Pout = gp * inv;
-  const float nll_c = static_cast<float>(sp->nll_const);
+  // -ln((1 - w_n) (2 pi s2)^(-3/2)): the pair's constant, or per source with confidences
+  float nll_c = static_cast<float>(sp->nll_const);
+  if (cf_x && valid) {
+    const float wn = 1.f - static_cast<float>(1.0 - sp->w0) * xw;
+    nll_c += static_cast<float>(sp->ln_1mw) - log1pf(-wn);
+  }
   const float nll = (valid && denom > 0.f) ? nll_c - (L * 0.6931471805599453f + logf(denom)) : 0.f;
   if (valid && per_n) {
     float4* o = reinterpret_cast<float4*>(per_n + (off64[pair] + local) * 16);
@@ -721,18 +732,19 @@ cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* ls_n,
-                         float* gam_n, cudaStream_t s) {
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int cf_x,
+                         float* ls_n, float* gam_n, cudaStream_t s) {
   const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
-  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.off64,
-                                                                      d.done_count, ls_n, gam_n, p.g);
+  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.done_count, cf_x,
+                                                                      ls_n, gam_n, p.g);
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
-                           const float* ls_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s) {
+                           int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
+                           cudaStream_t s) {
   combine_kernel<<<p.g.combine_ctas, kCombineThreads, 0, s>>>(xs, part, d.tab, d.off64, d.st, d.done_count,
-                                                              mode, ls_n, gam_n, rows, per_n, p.g);
+                                                              mode, cf_x, ls_n, gam_n, rows, per_n, p.g);
   return cudaGetLastError();
 }
 

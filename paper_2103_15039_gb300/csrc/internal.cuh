@@ -69,7 +69,9 @@ struct EmState {
   double nll_const;     // per-source constant of -log p: -ln((1-w) (2 pi s2)^(-3/2)) at the E step
   double log2_V;        // log2 V
   double ln_1mw;        // ln(1 - w)
-  double log2_pi;       // log2 pi_m of the uniform prior, -log2 M
+  double log2_pi;       // -log2 sum_m phi_m: log2 pi_m = log2 phi_m + log2_pi (uniform: -log2 M)
+  double w0;            // outlier weight w0 (given, or from the outlier ratio)
+  double nll_prev;      // NLL of the previous E step (termination on the likelihood)
   int32_t done;         // EM finished (floor, tol or numeric failure)
   int32_t iter;         // iterations completed
   int32_t numeric_fail;
@@ -81,12 +83,16 @@ struct EmState {
   float L;              // log2 gamma: the uniform log2 shift (-inf without outlier term)
   float sqc;            // sqrt(c): the E step's coordinate scale
   float lam;            // L - log2 pi: lambda_m of every target in the uniform-shift mode
+  float Lb;             // 1.5 log2(2 pi s2) - log2 V: log2 gamma_n = log2(w_n / (1 - w_n)) + Lb
+  float pad1;
 };
 
 // E-step constants for the current sigma2 (FP32: they feed FP32 arithmetic only).
 __device__ inline void set_sigma_constants(EmState* st, float s2) {
   const float lg = log2f(6.2831853f * s2);
-  const float L = static_cast<float>(st->log2_wodds) + 1.5f * lg - static_cast<float>(st->log2_V);
+  const float Lb = 1.5f * lg - static_cast<float>(st->log2_V);
+  const float L = static_cast<float>(st->log2_wodds) + Lb;
+  st->Lb = Lb;
   const float c = 1.44269504f / (2.f * s2);  // log2(e) / (2 s2)
   st->neg_c = -c;
   st->L = L;
@@ -115,7 +121,9 @@ struct DevParams {
   int32_t newton_max;
   int32_t include_alpha_norm;
   int32_t max_iters;
-  int32_t pad;
+  int32_t cf_x;         // per-source confidences phi_x present (carried in xs[n].w)
+  double eta;           // > 0: w0 from the outlier ratio
+  double nll_tol;       // > 0: stop on a small relative NLL change
 };
 
 // ---------------------------------------------------------------------------
@@ -182,13 +190,14 @@ struct Dev {
 // Rewrite the sigma-dependent record planes 0-3 from yl for the current state.
 cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, int mode, float* rec,
                             cudaStream_t s);
-// mode 1 only: L_n and gamma'_n of every source.
-cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, float* ls_n,
-                         float* gam_n, cudaStream_t s);
+// mode 1 only: L_n and gamma'_n of every source (cf_x: per-source w_n from xs[n].w).
+cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int cf_x,
+                         float* ls_n, float* gam_n, cudaStream_t s);
 cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode,
                          const float* ls_n, float* part, int* status, cudaStream_t s);
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
-                           const float* ls_n, const float* gam_n, double* rows, float* per_n, cudaStream_t s);
+                           int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
+                           cudaStream_t s);
 // Sum each pair's combine rows (fixed order, FP64) into mom[P][kGlob]; one warp per moment.
 cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom,
                                 cudaStream_t s);
@@ -210,16 +219,32 @@ int stats_chunks(const Geo& g);
 // Centroids, AABB, V, floor and centred sources of every pair; with `full`, also
 // sigma^2_0 and the initial EM state (otherwise only what the standalone E step
 // and the preprocessing need).
-cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const DevParams& dp,
-                        bool full, double* red, float4* xs, cudaStream_t s);
+// phi_x / phi_y (device, same offsets as X / Y) may be NULL (phi = 1); phi_x goes
+// to xs[n].w, sum phi_y sets the normalisation of pi(m).
+cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const float* phi_x,
+                        const float* phi_y, const DevParams& dp, bool full, double* red, float4* xs,
+                        cudaStream_t s);
 int knn_splits(const Geo& g, int num_sms);
 cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, int splits, float4* y4,
                        float* part_d, int* part_i, int* idx_out, cudaStream_t s);
+// Outlier weight from the outlier ratio (per pair, after the records exist):
+// w0 = eta V S / ((1 - eta) + eta V S), S = c0 sum_m 2^(l_m), then the E-step constants.
+cudaError_t launch_eta(const BatchPlan& p, const Dev& d, const float4* yl, double eta, cudaStream_t s);
+// Stable per-pair compaction of rows (x, y, z) whose phi >= threshold.  Pass 1
+// counts kept rows per (pair, chunk) into cnt[P][chunks]; pass 2 scatters with
+// the exclusive per-pair chunk offsets coff[P][chunks] (from the host) into
+// out rows at out_off[pair] + coff + rank, and phi into phi_out.
+int compact_chunks(long long max_rows);
+cudaError_t launch_compact_count(const float* phi, const long long* off, int P, int chunks, float threshold,
+                                 int* cnt, cudaStream_t s);
+cudaError_t launch_compact_scatter(const float* rows, const float* phi, const long long* off,
+                                   const long long* out_off, const int* coff, int P, int chunks, float threshold,
+                                   float* rows_out, float* phi_out, cudaStream_t s);
 // Both write the static record planes 4-15 and yl.
-cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
-                            double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
+cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const float* phi_y, const int* idx,
+                            int k, double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
                             float* normals, float* kappa, float* alpha, cudaStream_t s);
-cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals,
+cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* phi_y, const float* normals,
                         const float* alpha, int alpha_norm, float* rec, float4* yl, cudaStream_t s);
 
 }  // namespace lsg

@@ -535,7 +535,11 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     tr[7] = mom[74];
   }
   st->iter = it + 1;
-  if (done_sh || (dp.tol > 0.0 && motion < dp.tol)) {
+  // termination on the log-likelihood of Eq. (4): relative change since the previous E step
+  const double nll = mom[75];
+  const bool nll_stop = dp.nll_tol > 0.0 && it > 0 && fabs(nll - st->nll_prev) <= dp.nll_tol * fabs(nll);
+  st->nll_prev = nll;
+  if (done_sh || nll_stop || (dp.tol > 0.0 && motion < dp.tol)) {
     st->done = 1;
     atomicAdd(done_count, 1);
   }
@@ -583,6 +587,8 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
   st->log2_V = log2(V);
   st->log2_wodds = w > 0.0 ? log2(w) - log2(1.0 - w) : -INFINITY;
   st->ln_1mw = log1p(-w);
+  st->w0 = w;
+  st->nll_prev = 0.0;
   st->done = 0;
   st->iter = 0;
   st->numeric_fail = 0;

@@ -77,7 +77,7 @@ bool carve(unsigned char* base, const lsg::BatchPlan& p, Carve* c) {
   c->done_count = reinterpret_cast<int*>(take(sizeof(int)));
   c->tab = reinterpret_cast<int*>(take(sizeof(int) * p.tab.size()));
   c->off64 = reinterpret_cast<long long*>(take(sizeof(long long) * p.off64.size()));
-  c->red = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(lsg::stats_chunks(g)) * 20));
+  c->red = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(lsg::stats_chunks(g)) * 24));
   c->rows = reinterpret_cast<double*>(take(sizeof(double) * static_cast<size_t>(g.combine_ctas) * lsg::kGlob));
   c->mom = reinterpret_cast<double*>(take(sizeof(double) * lsg::kGlob));
   c->xs = reinterpret_cast<float4*>(take(sizeof(float4) * n_pad));
@@ -159,9 +159,9 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
   lsg::DevParams dp{};
   dp.w = p->w;
   dp.volume = volume;
-  if (e == cudaSuccess) e = lsg::launch_init(plan, d, X, Y, dp, false, c.red, c.xs, s);
+  if (e == cudaSuccess) e = lsg::launch_init(plan, d, X, Y, nullptr, nullptr, dp, false, c.red, c.xs, s);
   if (e == cudaSuccess) e = lsg::launch_estep_constants(c.st, sigma2, p->w, volume, R, t, s);
-  if (e == cudaSuccess) e = lsg::launch_pack(plan, d, Y, normals, alpha, p->include_alpha_norm, c.rec, c.yl, s);
+  if (e == cudaSuccess) e = lsg::launch_pack(plan, d, Y, nullptr, normals, alpha, p->include_alpha_norm, c.rec, c.yl, s);
   // fixed shift unless the outlier term is absent, a term could overflow FP32 or l_m varies
   int mode = 1;
   if (p->w > 0.0 && !p->include_alpha_norm) {
@@ -170,9 +170,9 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
     mode = (l_max - L + log2(static_cast<double>(M)) + 12.0 < 126.0) ? 0 : 1;
   }
   if (e == cudaSuccess) e = lsg::launch_prescale(plan, d, c.yl, mode, c.rec, s);
-  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, c.ls, c.gam, s);
+  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, 0, c.ls, c.gam, s);
   if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode, c.ls, c.part, c.status, s);
-  if (e == cudaSuccess) e = lsg::launch_combine(plan, d, c.xs, c.part, mode, c.ls, c.gam, c.rows, per_n, s);
+  if (e == cudaSuccess) e = lsg::launch_combine(plan, d, c.xs, c.part, mode, 0, c.ls, c.gam, c.rows, per_n, s);
   if (e == cudaSuccess) e = lsg::launch_final_reduce(plan, d, c.rows, c.mom, s);
   double mom[LSGCPD_MOMENTS];
   double mu[3];

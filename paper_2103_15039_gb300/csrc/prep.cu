@@ -61,8 +61,10 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* out_r
 }
 
 // Pass 1 (per pair, per chunk of kStatChunk points): sum x (3), sum y (3),
-// min y (3), max y (3).  grid = (chunks, P).
+// min y (3), max y (3), sum phi_y.  grid = (chunks, P).
+constexpr int kRaw = 13;
 __global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                                                 const float* __restrict__ phi_y,
                                                                  const long long* __restrict__ off64, int P,
                                                                  double* __restrict__ red) {
   const int pair = blockIdx.y;
@@ -70,11 +72,12 @@ __global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __
   const long long m0 = off64[P + 1 + pair], M = off64[P + 1 + pair + 1] - m0;
   const long long c0 = static_cast<long long>(blockIdx.x) * kStatChunk;
   if (c0 >= (N > M ? N : M)) return;
-  double v[12];
-  const int op[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2};
+  double v[kRaw];
+  const int op[kRaw] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 0};
   for (int j = 0; j < 6; ++j) v[j] = 0.0;
   for (int j = 6; j < 9; ++j) v[j] = INFINITY;
   for (int j = 9; j < 12; ++j) v[j] = -INFINITY;
+  v[12] = 0.0;
   for (long long i = c0 + threadIdx.x; i < c0 + kStatChunk; i += kStatThreads) {
     if (i < N) {
       const float* x = X + 3 * (n0 + i);
@@ -94,27 +97,28 @@ __global__ void __launch_bounds__(kStatThreads) raw_stats_kernel(const float* __
       v[9] = fmax(v[9], a);
       v[10] = fmax(v[10], b);
       v[11] = fmax(v[11], c);
+      v[12] += phi_y ? static_cast<double>(phi_y[m0 + i]) : 1.0;
     }
   }
-  block_reduce<12>(v, op, red + (static_cast<size_t>(pair) * gridDim.x + blockIdx.x) * 12);
+  block_reduce<kRaw>(v, op, red + (static_cast<size_t>(pair) * gridDim.x + blockIdx.x) * kRaw);
 }
 
 // Finalise pass 1 per pair (grid = P, one warp per value): centroids, V,
 // diagonal and sigma^2 floor.
 __global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, const long long* __restrict__ off64,
                                     int P, double volume, double floor_rel, EmState* __restrict__ st_all) {
-  __shared__ double v[12];
+  __shared__ double v[kRaw];
   const int pair = blockIdx.x;
   const long long N = off64[pair + 1] - off64[pair];
   const long long M = off64[P + 1 + pair + 1] - off64[P + 1 + pair];
   const long long big = N > M ? N : M;
   const int nchunk = static_cast<int>((big + kStatChunk - 1) / kStatChunk);
   const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (j < 12) {
-    const int op = j < 6 ? 0 : (j < 9 ? 1 : 2);
+  if (j < kRaw) {
+    const int op = (j < 6 || j == 12) ? 0 : (j < 9 ? 1 : 2);
     double x = op == 0 ? 0.0 : (op == 1 ? INFINITY : -INFINITY);
     for (int b = lane; b < nchunk; b += 32) {
-      const double r = red[(static_cast<size_t>(pair) * chunks + b) * 12 + j];
+      const double r = red[(static_cast<size_t>(pair) * chunks + b) * kRaw + j];
       x = op == 0 ? x + r : (op == 1 ? fmin(x, r) : fmax(x, r));
     }
     x = op == 0 ? warp_sum_d(x) : (op == 1 ? warp_min_d(x) : warp_max_d(x));
@@ -136,7 +140,7 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, 
   double V = 1.0;
   for (int c = 0; c < 3; ++c) V *= fmax(s[c], 1e-2 * diag);
   st->diag = diag;
-  st->log2_pi = -log2(static_cast<double>(M));
+  st->log2_pi = -log2(v[12]);  // pi(m) = phi_m / sum phi (phi = 1: 1 / M)
   st->V = volume > 0.0 ? volume : V;
   st->sigma2_floor = floor_rel * diag * diag;
 }
@@ -145,6 +149,7 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, 
 // to the pair's whole source blocks) and sums of the centred clouds:
 // sum xc (3), sum |xc|^2, sum yc (3), sum |yc|^2.
 __global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __restrict__ X, const float* __restrict__ Y,
+                                                              const float* __restrict__ phi_x,
                                                               const long long* __restrict__ off64,
                                                               const int* __restrict__ tab, Geo g,
                                                               const EmState* __restrict__ st_all,
@@ -170,13 +175,13 @@ __global__ void __launch_bounds__(kStatThreads) center_kernel(const float* __res
         const float* x = X + 3 * (n0 + i);
         const float fa = static_cast<float>(x[0] - mx0), fb = static_cast<float>(x[1] - mx1),
                     fc = static_cast<float>(x[2] - mx2);
-        xs[xb + i] = make_float4(fa, fb, fc, 0.f);
+        xs[xb + i] = make_float4(fa, fb, fc, phi_x ? phi_x[n0 + i] : 1.f);
         v[0] += fa;
         v[1] += fb;
         v[2] += fc;
         v[3] += static_cast<double>(fa) * fa + static_cast<double>(fb) * fb + static_cast<double>(fc) * fc;
       } else {
-        xs[xb + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        xs[xb + i] = make_float4(0.f, 0.f, 0.f, 1.f);
       }
     }
     if (i < M) {
@@ -243,6 +248,8 @@ __global__ void finalize_init_kernel(const double* __restrict__ red, int chunks,
   st->log2_wodds = dp.w > 0.0 ? log2(dp.w) - log2(1.0 - dp.w) : -INFINITY;
   st->log2_V = log2(st->V);
   st->ln_1mw = log1p(-dp.w);
+  st->w0 = dp.w;
+  st->nll_prev = 0.0;
   st->done = 0;
   st->iter = 0;
   st->numeric_fail = 0;
@@ -454,9 +461,10 @@ __device__ __forceinline__ void write_padding(float* rec, float4* yl, long long 
 // coordinates, a = sqrt(alpha) n, b = Lambda y_c = y_c + (a . y_c) a (FP64, then FP32).
 __device__ __forceinline__ void pack_target(float* rec, float4* yl, long long slot, const float* y,
                                             const EmState* st, double nx, double ny, double nz, double alpha,
-                                            double log2_pi, int alpha_norm) {
+                                            double phi, int alpha_norm) {
   const double sa = sqrt(alpha > 0.0 ? alpha : 0.0);
-  const double l = log2_pi + (alpha_norm ? 0.5 * log2(1.0 + alpha) : 0.0);
+  // l_m = log2 pi(m) (+ 1/2 log2(1 + alpha_m)), pi(m) = phi_m / sum phi
+  const double l = (phi == 1.0 ? 0.0 : log2(phi)) + st->log2_pi + (alpha_norm ? 0.5 * log2(1.0 + alpha) : 0.0);
   const double c0 = y[0] - st->mu_y[0], c1 = y[1] - st->mu_y[1], c2 = y[2] - st->mu_y[2];
   const double a0 = sa * nx, a1 = sa * ny, a2 = sa * nz;
   const double ay = a0 * c0 + a1 * c1 + a2 * c2;
@@ -469,6 +477,7 @@ __device__ __forceinline__ void pack_target(float* rec, float4* yl, long long sl
 // grid = (largest tile count, P), kTile threads: target m = tile * kTile + tid of
 // the pair; its record slot is (tile_off[pair] + tile) * kTile + tid.
 __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict__ Y,
+                                                         const float* __restrict__ phi_y,
                                                          const long long* __restrict__ off64,
                                                          const int* __restrict__ tab, Geo g,
                                                          const int* __restrict__ idx, int k, double alpha_max,
@@ -525,7 +534,7 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
   }
   double a = kap > 0.0 ? alpha_max * tanh(0.5 * lambda * (1.0 / kap - 3.0)) : alpha_max;
   if (a < 0.0) a = 0.0;
-  pack_target(rec, yl, slot, Y + 3 * gm, st_all + pair, n0, n1, n2, a, st_all[pair].log2_pi, alpha_norm);
+  pack_target(rec, yl, slot, Y + 3 * gm, st_all + pair, n0, n1, n2, a, phi_y ? phi_y[gm] : 1.0, alpha_norm);
   if (normals) {
     normals[3 * gm] = static_cast<float>(n0);
     normals[3 * gm + 1] = static_cast<float>(n1);
@@ -535,7 +544,8 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
   if (alpha_out) alpha_out[gm] = static_cast<float>(a);
 }
 
-__global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y, const long long* __restrict__ off64,
+__global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y, const float* __restrict__ phi_y,
+                                                     const long long* __restrict__ off64,
                                                      const int* __restrict__ tab, Geo g,
                                                      const float* __restrict__ normals, const float* __restrict__ alpha,
                                                      int alpha_norm, const EmState* __restrict__ st_all,
@@ -553,7 +563,100 @@ __global__ void __launch_bounds__(kTile) pack_kernel(const float* __restrict__ Y
   }
   const long long gm = m0 + m;
   pack_target(rec, yl, slot, Y + 3 * gm, st_all + pair, normals[3 * gm], normals[3 * gm + 1], normals[3 * gm + 2],
-              alpha[gm], st_all[pair].log2_pi, alpha_norm);
+              alpha[gm], phi_y ? phi_y[gm] : 1.0, alpha_norm);
+}
+
+// Outlier weight from the outlier ratio (Sec. 3.2), one CTA per pair:
+// S = sum_m pi(m) c_m = c0 sum_m 2^(l_m) with c0 = (2 pi sigma^2_0)^(-3/2) (l_m
+// already holds log2 pi(m) and, with the Gaussian constant, 1/2 log2(1 + alpha_m)),
+// w0 = eta V S / ((1 - eta) + eta V S), then the E-step constants of the pair.
+constexpr int kEtaThreads = 256;
+__global__ void __launch_bounds__(kEtaThreads) eta_kernel(const float4* __restrict__ yl, const int* __restrict__ tab,
+                                                          Geo g, double eta, EmState* __restrict__ st_all) {
+  __shared__ double sh[kEtaThreads / 32];
+  const int pair = blockIdx.x;
+  const long long s0 = static_cast<long long>(tab[g.o_tile_off + pair]) * kTile;
+  const long long s1 = static_cast<long long>(tab[g.o_tile_off + pair + 1]) * kTile;
+  double acc = 0.0;
+  for (long long i = s0 + threadIdx.x; i < s1; i += kEtaThreads) acc += exp2(static_cast<double>(yl[i].w));
+  acc = warp_sum_d(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sum = 0.0;
+  for (int w = 0; w < kEtaThreads / 32; ++w) sum += sh[w];
+  EmState* st = st_all + pair;
+  const double S = pow(2.0 * 3.14159265358979323846 * st->sigma2, -1.5) * sum;
+  const double a = eta * st->V * S;
+  const double w = a / ((1.0 - eta) + a);
+  st->w0 = w;
+  st->log2_wodds = w > 0.0 ? log2(w) - log2(1.0 - w) : -INFINITY;
+  st->ln_1mw = log1p(-w);
+  set_estep_constants(st);
+}
+
+// Stable compaction (confidence truncation, Sec. 3.3).  grid = (chunks, P),
+// kStatThreads threads, kStatChunk rows per CTA: each thread owns two
+// consecutive rows, so ranks follow from one block-wide exclusive scan.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int wsum[kStatThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int before = 0, all = 0;
+  for (int w = 0; w < kStatThreads / 32; ++w) {
+    if (w < warp) before += wsum[w];
+    all += wsum[w];
+  }
+  __syncthreads();
+  *total = all;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kStatThreads) compact_count_kernel(const float* __restrict__ phi,
+                                                                     const long long* __restrict__ off, float thr,
+                                                                     int* __restrict__ cnt) {
+  const int pair = blockIdx.y;
+  const long long r0 = off[pair], n = off[pair + 1] - r0;
+  const long long i0 = static_cast<long long>(blockIdx.x) * kStatChunk + 2 * threadIdx.x;
+  int v = 0;
+  for (int j = 0; j < 2; ++j)
+    if (i0 + j < n && phi[r0 + i0 + j] >= thr) ++v;
+  int total = 0;
+  block_exclusive_scan(v, &total);
+  if (threadIdx.x == 0) cnt[static_cast<size_t>(pair) * gridDim.x + blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kStatThreads) compact_scatter_kernel(
+    const float* __restrict__ rows, const float* __restrict__ phi, const long long* __restrict__ off,
+    const long long* __restrict__ out_off, const int* __restrict__ coff, float thr, float* __restrict__ rows_out,
+    float* __restrict__ phi_out) {
+  const int pair = blockIdx.y;
+  const long long r0 = off[pair], n = off[pair + 1] - r0;
+  const long long i0 = static_cast<long long>(blockIdx.x) * kStatChunk + 2 * threadIdx.x;
+  bool keep[2];
+  int v = 0;
+  for (int j = 0; j < 2; ++j) {
+    keep[j] = i0 + j < n && phi[r0 + i0 + j] >= thr;
+    v += keep[j];
+  }
+  int total = 0;
+  int rank = block_exclusive_scan(v, &total);
+  const long long o0 = out_off[pair] + coff[static_cast<size_t>(pair) * gridDim.x + blockIdx.x];
+  for (int j = 0; j < 2; ++j)
+    if (keep[j]) {
+      const long long src = r0 + i0 + j, dst = o0 + rank++;
+      rows_out[3 * dst] = rows[3 * src];
+      rows_out[3 * dst + 1] = rows[3 * src + 1];
+      rows_out[3 * dst + 2] = rows[3 * src + 2];
+      phi_out[dst] = phi[src];
+    }
 }
 
 }  // namespace
@@ -564,16 +667,17 @@ int stats_chunks(const Geo& g) {
   return static_cast<int>((big + kStatChunk - 1) / kStatChunk);
 }
 
-cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const DevParams& dp,
-                        bool full, double* red, float4* xs, cudaStream_t s) {
+cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const float* Y, const float* phi_x,
+                        const float* phi_y, const DevParams& dp, bool full, double* red, float4* xs,
+                        cudaStream_t s) {
   const Geo& g = p.g;
   const int chunks = stats_chunks(g);
   dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(g.P));
-  raw_stats_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, d.off64, g.P, red);
-  finalize_raw_kernel<<<g.P, 12 * 32, 0, s>>>(red, chunks, d.off64, g.P, full ? dp.volume : 0.0,
+  raw_stats_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, phi_y, d.off64, g.P, red);
+  finalize_raw_kernel<<<g.P, kRaw * 32, 0, s>>>(red, chunks, d.off64, g.P, full ? dp.volume : 0.0,
                                               full ? dp.sigma2_floor_rel : 0.0, d.st);
-  double* red2 = red + static_cast<size_t>(g.P) * chunks * 12;
-  center_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, d.off64, d.tab, g, d.st, xs, red2);
+  double* red2 = red + static_cast<size_t>(g.P) * chunks * kRaw;
+  center_kernel<<<grid, kStatThreads, 0, s>>>(X, Y, phi_x, d.off64, d.tab, g, d.st, xs, red2);
   if (full) finalize_init_kernel<<<g.P, 8 * 32, 0, s>>>(red2, chunks, d.off64, d.tab, g, dp, d.st, d.done_count);
   return cudaGetLastError();
 }
@@ -613,19 +717,41 @@ cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const int* idx, int k,
-                            double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
+cudaError_t launch_geometry(const BatchPlan& p, const Dev& d, const float* Y, const float* phi_y, const int* idx,
+                            int k, double alpha_max, double lambda, int alpha_norm, float* rec, float4* yl,
                             float* normals, float* kappa, float* alpha, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
-  geometry_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, idx, k, alpha_max, lambda, alpha_norm, d.st, rec,
+  geometry_kernel<<<grid, kTile, 0, s>>>(Y, phi_y, d.off64, d.tab, p.g, idx, k, alpha_max, lambda, alpha_norm, d.st, rec,
                                          yl, normals, kappa, alpha);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* normals, const float* alpha,
-                        int alpha_norm, float* rec, float4* yl, cudaStream_t s) {
+cudaError_t launch_pack(const BatchPlan& p, const Dev& d, const float* Y, const float* phi_y, const float* normals,
+                        const float* alpha, int alpha_norm, float* rec, float4* yl, cudaStream_t s) {
   dim3 grid(static_cast<unsigned>(p.g.max_tiles), static_cast<unsigned>(p.g.P));
-  pack_kernel<<<grid, kTile, 0, s>>>(Y, d.off64, d.tab, p.g, normals, alpha, alpha_norm, d.st, rec, yl);
+  pack_kernel<<<grid, kTile, 0, s>>>(Y, phi_y, d.off64, d.tab, p.g, normals, alpha, alpha_norm, d.st, rec, yl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta(const BatchPlan& p, const Dev& d, const float4* yl, double eta, cudaStream_t s) {
+  eta_kernel<<<p.g.P, kEtaThreads, 0, s>>>(yl, d.tab, p.g, eta, d.st);
+  return cudaGetLastError();
+}
+
+int compact_chunks(long long max_rows) { return static_cast<int>((max_rows + kStatChunk - 1) / kStatChunk); }
+
+cudaError_t launch_compact_count(const float* phi, const long long* off, int P, int chunks, float threshold,
+                                 int* cnt, cudaStream_t s) {
+  dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(P));
+  compact_count_kernel<<<grid, kStatThreads, 0, s>>>(phi, off, threshold, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_scatter(const float* rows, const float* phi, const long long* off,
+                                   const long long* out_off, const int* coff, int P, int chunks, float threshold,
+                                   float* rows_out, float* phi_out, cudaStream_t s) {
+  dim3 grid(static_cast<unsigned>(chunks), static_cast<unsigned>(P));
+  compact_scatter_kernel<<<grid, kStatThreads, 0, s>>>(rows, phi, off, out_off, coff, threshold, rows_out, phi_out);
   return cudaGetLastError();
 }
 

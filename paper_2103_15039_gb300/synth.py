@@ -371,8 +371,20 @@ def rgbd_room_pair(seed=SEED_BASE + 2, overlap=0.70, overlap_tol=0.03, max_angle
     P = noisy_view(c2, R2)
     R_p = random_rotation(rng, math.radians(rng.uniform(0.0, max_angle_deg)))
     t_p = rng.uniform(0.0, max_trans) * random_unit_vector(rng)
-    return _pair(Y, P, R_p, t_p, P.mean(axis=0), name="rgbd_room", seed=seed, w=0.1, knn_k=10,
-                 max_iters=50, overlap=frac)
+    centre = P.mean(axis=0)
+    cam_source = R_p @ (c2 - centre) + centre + t_p  # the source camera moves with its view
+    return _pair(Y, P, R_p, t_p, centre, name="rgbd_room", seed=seed, w=0.1, knn_k=10,
+                 max_iters=50, overlap=frac, cam_target=c1, cam_source=cam_source)
+
+
+def depth_confidence(points, camera, near=None):
+    """Measurement confidence phi = e_min / e(x) for a depth sensor whose error
+    grows with the squared depth, e(x) = k max(|x - camera|, near)^2 (k cancels),
+    e_min = k near^2 the error at the sensor's near limit (default: the 5th
+    percentile of the view's depths).  float32 in (0, 1]."""
+    d = np.sqrt(((np.asarray(points, dtype=np.float64) - np.asarray(camera)) ** 2).sum(axis=1))
+    near = float(np.percentile(d, 5.0)) if near is None else float(near)
+    return np.minimum(1.0, (near / np.maximum(d, 1e-12)) ** 2).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------
