@@ -66,9 +66,31 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(offset, rank):
+    """Seed of rank `rank`'s independent problem (weak scaling: every rank its own pair)."""
+    from paper_2103_15039_gb300 import synth
+    return synth.SEED_BASE + offset + 1000 * rank
+
+
+def reduce_max(values, ws, device):
+    """Max over ranks of per-rank times (the job is as slow as its slowest rank)."""
+    if ws == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def job_throughput(units_per_rank, ws, ms):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / (ms / 1e3)
+
+
 def workload(rank):
     from paper_2103_15039_gb300 import synth
-    seed = synth.SEED_BASE + 2 + 1000 * rank
+    seed = rank_seed(2, rank)
     c = synth.rgbd_room_pair(seed=seed)
     return c, seed
 
@@ -77,7 +99,7 @@ def batch_workload(rank):
     import numpy as np
 
     from paper_2103_15039_gb300 import synth
-    seed = synth.SEED_BASE + 4 + 1000 * rank
+    seed = rank_seed(4, rank)
     pairs = synth.batch_pairs(seed=seed)
     X = np.concatenate([q["X"] for q in pairs]).astype(np.float32)
     Y = np.concatenate([q["Y"] for q in pairs]).astype(np.float32)
@@ -285,15 +307,10 @@ def run_ours(args):
     xfer = ctx.last_timing()
     assert np.allclose(r["R"], got["R"]) and np.allclose(r["t"], got["t"])
 
-    ms = statistics.mean(step_ms)
-    e2e_ms = statistics.mean(e2e_s) * 1e3
-    if ws > 1:
-        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(tt[0]), float(tt[1])
+    ms, e2e_ms = reduce_max([statistics.mean(step_ms), statistics.mean(e2e_s) * 1e3], ws, "cuda")
     pairs_per_step = iters_run * N * M
-    value = ws * pairs_per_step / (ms / 1e3)
-    e2e_value = ws * pairs_per_step / (e2e_ms / 1e3)
+    value = job_throughput(pairs_per_step, ws, ms)
+    e2e_value = job_throughput(pairs_per_step, ws, e2e_ms)
 
     # roofline of the hot kernel (E step): per-launch time measured live
     t_launch = statistics.mean(estep_ms) / iters_run / 1e3
@@ -417,14 +434,9 @@ def run_batch(args):
     pp_ms = e0.elapsed_time(e1)
     pp_pairs = float(sum(s["iters"] * n for s, n in zip(singles, nm)))
 
-    ms = statistics.mean(step_ms)
-    e2e_ms = statistics.mean(e2e_s) * 1e3
-    if ws > 1:
-        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(tt[0]), float(tt[1])
-    value = ws * pairs_per_step / (ms / 1e3)
-    e2e_value = ws * pairs_per_step / (e2e_ms / 1e3)
+    ms, e2e_ms = reduce_max([statistics.mean(step_ms), statistics.mean(e2e_s) * 1e3], ws, "cuda")
+    value = job_throughput(pairs_per_step, ws, ms)
+    e2e_value = job_throughput(pairs_per_step, ws, e2e_ms)
     t_launch = statistics.mean(estep_ms) / iters_run / 1e3
     per_launch = float(nm.sum())
     sms = torch.cuda.get_device_properties(local).multi_processor_count
