@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("volume", C.c_double), ("sigma2_init", C.c_double), ("init_R", C.c_double * 9),
         ("init_t", C.c_double * 3), ("newton_tol", C.c_double), ("sigma2_floor_rel", C.c_double),
         ("knn_k", C.c_int32), ("max_iters", C.c_int32), ("include_alpha_norm", C.c_int32),
-        ("newton_max", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("newton_max", C.c_int32), ("precision", C.c_int32), ("knn_method", C.c_int32),
         ("eta", C.c_double), ("cf_threshold", C.c_double), ("nll_tol", C.c_double),
         ("phi_x", C.c_void_p), ("phi_y", C.c_void_p),
     ]

@@ -50,6 +50,9 @@ struct lsgcpd_ctx {
   DevBuf<float> X_in, Y_in, rec, part, knn_d, ls_n, gam_n;
   DevBuf<float> phx_in, phy_in, Xc, Yc, phxc, phyc;  // confidences; truncated clouds
   DevBuf<int> cnt, coff;
+  DevBuf<int> g_count, g_start, g_fill, g_cellof, g_scan;  // grid kNN
+  DevBuf<float4> g_sorted;
+  DevBuf<double> g_info;
   DevBuf<long long> toff;
   DevBuf<float4> xs, y4, yl;
   DevBuf<int> knn_i, knn_idx, tab;
@@ -137,6 +140,7 @@ lsgcpd_status check_params(lsgcpd_ctx* c, const lsgcpd_params* p) {
   if (!is_finite_d(p->cf_threshold) || p->cf_threshold < 0.0)
     return fail(c, LSGCPD_EINVAL, "cf_threshold must be finite and >= 0");
   if (!is_finite_d(p->nll_tol) || p->nll_tol < 0.0) return fail(c, LSGCPD_EINVAL, "nll_tol must be finite and >= 0");
+  if (p->knn_method < 0 || p->knn_method > 2) return fail(c, LSGCPD_EINVAL, "knn_method must be 0, 1 or 2");
   return LSGCPD_OK;
 }
 
@@ -278,6 +282,30 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
 }
 
 Dev dev_of(lsgcpd_ctx* c) { return Dev{c->tab.p, c->off64.p, c->st.p, c->done_count}; }
+
+// k nearest targets of every target (needs the pair AABBs from launch_init for the grid).
+cudaError_t run_knn(lsgcpd_ctx* c, const BatchPlan& plan, const Dev& d, const float* Y, int k, int method,
+                    int* idx, int64_t* launches, cudaStream_t s) {
+  const bool grid = method == 2 || (method == 0 && plan.g.max_m > 50000);
+  if (!grid) {
+    *launches += 2;
+    return launch_knn(plan, d, Y, k, knn_splits(plan.g, c->num_sms), c->y4.p, c->knn_d.p, c->knn_i.p, idx, s);
+  }
+  const int P = plan.g.P;
+  const long long Mtot = plan.off64[2 * P + 1];
+  const long long cells = knn_grid_cells(Mtot, P);
+  cudaError_t e = ensure(c->g_count, static_cast<size_t>(cells));
+  if (e == cudaSuccess) e = ensure(c->g_fill, static_cast<size_t>(cells));
+  if (e == cudaSuccess) e = ensure(c->g_start, static_cast<size_t>(cells) + 1);
+  if (e == cudaSuccess) e = ensure(c->g_cellof, static_cast<size_t>(Mtot));
+  if (e == cudaSuccess) e = ensure(c->g_sorted, static_cast<size_t>(Mtot));
+  if (e == cudaSuccess) e = ensure(c->g_scan, knn_grid_scan_blocks(cells));
+  if (e == cudaSuccess) e = ensure(c->g_info, 8 * static_cast<size_t>(P));
+  if (e != cudaSuccess) return e;
+  const GridBufs gb{c->g_count.p, c->g_start.p, c->g_fill.p, c->g_cellof.p, c->g_sorted.p, c->g_scan.p, c->g_info.p};
+  *launches += 7;
+  return launch_knn_grid(plan, d, Y, k, gb, idx, s);
+}
 
 // The plan's tables and the finished-pair count (zero) for this call.  The
 // status word is cleared separately, before the input checks that set it.
@@ -528,12 +556,11 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   };
   LSG_CUDA(upload_plan(c, plan, s), "plan");
   LSG_CUDA(launch_init(plan, d, Xd, Yd, in.phx, in.phy, dp, true, c->red.p, c->xs.p, s), "init");
-  const int splits = knn_splits(plan.g, c->num_sms);
-  LSG_CUDA(launch_knn(plan, d, Yd, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, c->knn_idx.p, s), "knn");
+  LSG_CUDA(run_knn(c, plan, d, Yd, k, p->knn_method, c->knn_idx.p, &launches, s), "knn");
   LSG_CUDA(launch_geometry(plan, d, Yd, in.phy, c->knn_idx.p, k, p->alpha_max, p->lambda, p->include_alpha_norm,
                            c->rec.p, c->yl.p, nullptr, nullptr, nullptr, s),
            "geometry");
-  launches += 4 + 3 + 1;
+  launches += 4 + 1;
   if (p->eta > 0.0) {
     LSG_CUDA(launch_eta(plan, d, c->yl.p, p->eta, s), "eta");
     ++launches;
@@ -755,7 +782,9 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  void* bufs2[] = {c->phx_in.p, c->phy_in.p, c->Xc.p, c->Yc.p, c->phxc.p, c->phyc.p, c->cnt.p, c->coff.p, c->toff.p};
+  void* bufs2[] = {c->phx_in.p, c->phy_in.p, c->Xc.p,      c->Yc.p,       c->phxc.p,    c->phyc.p,   c->cnt.p,
+                   c->coff.p,   c->toff.p,   c->g_count.p, c->g_start.p,  c->g_fill.p,  c->g_cellof.p,
+                   c->g_scan.p, c->g_sorted.p, c->g_info.p};
   for (void* q : bufs2)
     if (q) cudaFree(q);
   void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->ls_n.p, c->gam_n.p,
@@ -827,14 +856,14 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   LSG_CUDA(check_finite(Y, M * 3, c->status, s), "check");
   const DevParams dp = dev_params(p);
   LSG_CUDA(launch_init(plan, d, Y, Y, nullptr, nullptr, dp, false, c->red.p, c->xs.p, s), "center");
-  const int splits = knn_splits(plan.g, c->num_sms);
   int* idx = knn_idx ? knn_idx : c->knn_idx.p;
-  LSG_CUDA(launch_knn(plan, d, Y, k, splits, c->y4.p, c->knn_d.p, c->knn_i.p, idx, s), "knn");
+  int64_t launches = 5;
+  LSG_CUDA(run_knn(c, plan, d, Y, k, p->knn_method, idx, &launches, s), "knn");
   LSG_CUDA(launch_geometry(plan, d, Y, nullptr, idx, k, p->alpha_max, p->lambda, p->include_alpha_norm, c->rec.p,
                            c->yl.p,
                            normals, kappa, alpha, s),
            "geometry");
-  c->launches = 7;
+  c->launches = launches;
   int status = 0;
   LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "status");
   LSG_CUDA(cudaStreamSynchronize(s), "sync");

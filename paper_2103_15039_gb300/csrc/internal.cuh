@@ -66,6 +66,8 @@ struct EmState {
   double log2_wodds;    // log2(w / (1 - w)); -inf when w = 0
   double mu_x[3];       // source centroid
   double mu_y[3];       // target centroid
+  double ylo[3];        // target AABB (caller's frame)
+  double yhi[3];
   double nll_const;     // per-source constant of -log p: -ln((1-w) (2 pi s2)^(-3/2)) at the E step
   double log2_V;        // log2 V
   double ln_1mw;        // ln(1 - w)
@@ -225,6 +227,22 @@ cudaError_t launch_init(const BatchPlan& p, const Dev& d, const float* X, const 
                         const float* phi_y, const DevParams& dp, bool full, double* red, float4* xs,
                         cudaStream_t s);
 int knn_splits(const Geo& g, int num_sms);
+// Exact kNN through a uniform grid per pair (same lists as launch_knn: FP32
+// distances, (distance, index) order).  Cells of pair i occupy
+// [4 m_off[i] + 64 i, 4 m_off[i+1] + 64 (i+1)) of the cell arrays.
+long long knn_grid_cells(long long Mtot, int P);
+struct GridBufs {
+  int* count;      // [cells] points per cell
+  int* start;      // [cells + 1] exclusive prefix of count (global sorted position)
+  int* fill;       // [cells] scatter cursor
+  int* cell_of;    // [Mtot] cell of every target
+  float4* sorted;  // [Mtot] targets sorted by cell, w = pair-local index (bits)
+  int* scan_tmp;   // [scan blocks] block sums
+  double* info;    // [P][8] grid origin (3), cell edge, dims (3)
+};
+size_t knn_grid_scan_blocks(long long cells);
+cudaError_t launch_knn_grid(const BatchPlan& p, const Dev& d, const float* Y, int k, const GridBufs& gb,
+                            int* idx_out, cudaStream_t s);
 cudaError_t launch_knn(const BatchPlan& p, const Dev& d, const float* Y, int k, int splits, float4* y4,
                        float* part_d, int* part_i, int* idx_out, cudaStream_t s);
 // Outlier weight from the outlier ratio (per pair, after the records exist):

@@ -140,6 +140,10 @@ __global__ void finalize_raw_kernel(const double* __restrict__ red, int chunks, 
   double V = 1.0;
   for (int c = 0; c < 3; ++c) V *= fmax(s[c], 1e-2 * diag);
   st->diag = diag;
+  for (int c = 0; c < 3; ++c) {
+    st->ylo[c] = v[6 + c];
+    st->yhi[c] = v[9 + c];
+  }
   st->log2_pi = -log2(v[12]);  // pi(m) = phi_m / sum phi (phi = 1: 1 / M)
   st->V = volume > 0.0 ? volume : V;
   st->sigma2_floor = floor_rel * diag * diag;

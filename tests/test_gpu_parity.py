@@ -178,3 +178,39 @@ def test_knn_exact_ties_keep_the_lower_index(ctx):
     p = binding.default_params(knn_k=7)
     g = ctx.preprocess(_cuda(Y), p, want_idx=True)
     np.testing.assert_array_equal(g["idx"].cpu().numpy(), oracle.knn(Y, 7))
+
+
+@pytest.mark.parametrize("shape", ["uniform", "lattice", "plane", "clusters", "duplicates"])
+@pytest.mark.parametrize("k", [1, 4, 10, 16, 20, 32])
+def test_grid_knn_equals_bruteforce(ctx, shape, k):
+    """The uniform-grid search returns the brute-force lists, ties included."""
+    rng = np.random.default_rng(31)
+    Y = {"uniform": rng.uniform(-1, 1, (3000, 3)),
+         "lattice": np.stack(np.meshgrid(*[np.arange(13)] * 3), -1).reshape(-1, 3) * 0.25,
+         "plane": np.c_[rng.uniform(0, 1, (2500, 2)), np.zeros(2500)],
+         "clusters": np.concatenate([rng.normal(c, 0.01, (500, 3)) for c in rng.uniform(-5, 5, (5, 3))]),
+         "duplicates": np.repeat(rng.uniform(0, 1, (300, 3)), 4, axis=0)}[shape].astype(np.float32)
+    p = binding.default_params(knn_k=k, knn_method=2)
+    g = ctx.preprocess(_cuda(Y), p, want_idx=True)
+    np.testing.assert_array_equal(g["idx"].cpu().numpy(), oracle.knn(Y, k, method="brute"))
+
+
+def test_grid_and_bruteforce_knn_agree_on_the_rgbd_target(ctx):
+    Y = synth.rgbd_room_pair()["Y"]
+    a = ctx.preprocess(_cuda(Y), binding.default_params(knn_method=1), want_idx=True)
+    b = ctx.preprocess(_cuda(Y), binding.default_params(knn_method=2), want_idx=True)
+    np.testing.assert_array_equal(a["idx"].cpu().numpy(), b["idx"].cpu().numpy())
+    np.testing.assert_array_equal(a["alpha"].cpu().numpy(), b["alpha"].cpu().numpy())
+
+
+def test_grid_knn_in_a_batch(ctx):
+    """Per-pair grids: lists never cross pairs and equal each pair's own search."""
+    pairs = synth.batch_pairs(num_pairs=6, n_lo=40, n_hi=3000)
+    X = np.concatenate([q["X"] for q in pairs])
+    Y = np.concatenate([q["Y"] for q in pairs])
+    n_off = np.concatenate([[0], np.cumsum([len(q["X"]) for q in pairs])])
+    m_off = np.concatenate([[0], np.cumsum([len(q["Y"]) for q in pairs])])
+    a = ctx.register_batch(X, n_off, Y, m_off, binding.default_params(max_iters=3, knn_method=1))
+    b = ctx.register_batch(X, n_off, Y, m_off, binding.default_params(max_iters=3, knn_method=2))
+    np.testing.assert_array_equal(a["R"], b["R"])
+    np.testing.assert_array_equal(a["t"], b["t"])
