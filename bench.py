@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["rgbd20k", "batch256"], default="rgbd20k")
+    ap.add_argument("--precision", type=int, choices=[0, 1], default=0,
+                    help="0: FP32 E step; 1: f16x2 exponentials (mixed precision)")
     return ap.parse_args()
 
 
@@ -108,10 +110,11 @@ def batch_workload(rank):
     return pairs, X, n_off, Y, m_off, seed
 
 
-def config_obj(c, seed, iters, n_gpus):
+def config_obj(c, seed, iters, n_gpus, precision=0):
     return {"workload": "rgbd_room_20000x20000", "N": int(len(c["X"])), "M": int(len(c["Y"])),
             "em_iters": iters, "knn_k": 10, "w": 0.1, "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
-            "overlap": round(float(c["overlap"]), 4), "e_step": "fp32 (packed f32x2) + ex2.approx",
+            "overlap": round(float(c["overlap"]), 4),
+            "e_step": "fp32 (packed f32x2) + ex2.approx" if precision == 0 else "fp32 residuals + f16x2 ex2.approx",
             "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus} (independent pairs per GPU)"}
 
@@ -257,7 +260,7 @@ def run_ours(args):
     N, M = len(c["X"]), len(c["Y"])
     iters = args.iters
     ctx = binding.Context(local, N, M)
-    p = binding.default_params(max_iters=iters)
+    p = binding.default_params(max_iters=iters, precision=args.precision)
     Xd = torch.from_numpy(c["X"]).cuda()
     Yd = torch.from_numpy(c["Y"]).cuda()
     Xh = torch.from_numpy(c["X"]).pin_memory()
@@ -330,8 +333,8 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": config_obj(c, seed, iters, ws),
+           "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f16", "data": "synthetic",
+           "config": config_obj(c, seed, iters, ws, args.precision),
            "em_iters_per_s": ws * iters_run / (ms / 1e3),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4),
@@ -369,7 +372,7 @@ def run_batch(args):
     nm = (Ns * Ms).astype(np.float64)
     iters = args.iters
     ctx = binding.Context(local, int(Ns.max()), int(Ms.max()))
-    p = binding.default_params(max_iters=iters)
+    p = binding.default_params(max_iters=iters, precision=args.precision)
     Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
     Xh, Yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -449,10 +452,12 @@ def run_batch(args):
             "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f16", "data": "synthetic",
            "config": {"workload": "batch_256_pairs_500_20000", "pairs": P, "sum_N": int(Ns.sum()),
                       "sum_M": int(Ms.sum()), "sum_NM": int(nm.sum()), "em_iters": iters, "knn_k": 10, "w": 0.1,
-                      "alpha_max": 2.0, "lambda": 0.2, "seed": seed, "e_step": "fp32 (packed f32x2) + ex2.approx",
+                      "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
+                      "e_step": "fp32 (packed f32x2) + ex2.approx" if args.precision == 0
+                      else "fp32 residuals + f16x2 ex2.approx",
                       "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
                       "parallelism": f"replicas x{ws} (independent batches per GPU)"},
            "em_iters_per_s": ws * iters_run / (ms / 1e3),

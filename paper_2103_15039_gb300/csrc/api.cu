@@ -32,10 +32,10 @@ struct DevBuf {
 struct GraphKey {
   std::vector<long long> sizes;
   std::vector<unsigned char> params;
-  int iters = -1, mode = -1, S = -1, timing = -1, trace = -1;
+  int iters = -1, mode = -1, half = -1, S = -1, timing = -1, trace = -1;
   bool operator==(const GraphKey& o) const {
-    return sizes == o.sizes && params == o.params && iters == o.iters && mode == o.mode && S == o.S &&
-           timing == o.timing && trace == o.trace;
+    return sizes == o.sizes && params == o.params && iters == o.iters && mode == o.mode && half == o.half &&
+           S == o.S && timing == o.timing && trace == o.trace;
   }
 };
 
@@ -135,7 +135,8 @@ lsgcpd_status check_params(lsgcpd_ctx* c, const lsgcpd_params* p) {
     return fail(c, LSGCPD_EINVAL, "sigma2_floor_rel must be >= 0");
   if (p->max_iters < 0 || p->max_iters > 100000) return fail(c, LSGCPD_EINVAL, "max_iters out of range");
   if (p->newton_max < 1 || p->newton_max > 1000) return fail(c, LSGCPD_EINVAL, "newton_max out of range");
-  if (p->precision != 0) return fail(c, LSGCPD_EINVAL, "only precision 0 (FP32 E step) is implemented");
+  if (p->precision != 0 && p->precision != 1)
+    return fail(c, LSGCPD_EINVAL, "precision must be 0 (FP32) or 1 (f16x2 exponentials)");
   if (!(p->eta >= 0.0 && p->eta < 1.0)) return fail(c, LSGCPD_EINVAL, "eta must be in [0, 1)");
   if (!is_finite_d(p->cf_threshold) || p->cf_threshold < 0.0)
     return fail(c, LSGCPD_EINVAL, "cf_threshold must be finite and >= 0");
@@ -578,7 +579,8 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   // one shift mode for the whole batch: fixed shift only if it is safe for every pair, l_m is
   // uniform (the uniform-shift moments assume one l) and w_n is uniform
   const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
-  int mode = (p->include_alpha_norm || in.phx || in.phy) ? 1 : 0;
+  int mode = (p->include_alpha_norm || in.phx || in.phy || p->precision == 1) ? 1 : 0;
+  const int half = p->precision == 1 ? 1 : 0;
   for (int i = 0; i < P; ++i) mode |= choose_mode(hs[i].w0, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
   const int cfx = in.phx ? 1 : 0;
   if (tune) {
@@ -590,10 +592,10 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       LSG_CUDA(upload_plan(c, pc, s), "plan");
       LSG_CUDA(init_state(pc), "init");
       LSG_CUDA(launch_prescale(pc, d, c->yl.p, mode, c->rec.p, s), "prescale");
-      if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s), "shift");
-      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
+      if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s), "shift");
+      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[0], s), "event");
-      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
+      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[1], s), "event");
       LSG_CUDA(cudaEventSynchronize(c->tune_ev[1]), "sync");
       const double ms = elapsed_ms(c->tune_ev[0], c->tune_ev[1]);
@@ -602,7 +604,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         best = ms;
         rec.S = pc.g.S;
       }
-      launches += (mode ? 4 : 3);
+      launches += (mode ? 5 : 3);
     }
     for (const BatchPlan& pc : cands)
       if (pc.g.S == rec.S) plan = pc;
@@ -625,6 +627,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
                       reinterpret_cast<const unsigned char*>(&dp) + sizeof(dp));
     key.iters = iters;
     key.mode = mode;
+    key.half = half;
     key.S = g.S;
     key.timing = c->timing;
     key.trace = trace ? 1 : 0;
@@ -640,8 +643,8 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
         if (ce == cudaSuccess) ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
         if (ce == cudaSuccess && mode == 1)
-          ce = launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s);
-        if (ce == cudaSuccess) ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s);
+          ce = launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s);
+        if (ce == cudaSuccess) ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
@@ -668,7 +671,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       c->gkey = key;
     }
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * (mode ? 6 : 5);
+    launches += static_cast<int64_t>(iters) * (mode ? 7 : 5);
   }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");
@@ -913,15 +916,17 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
   LSG_CUDA(launch_pack(plan, d, Y, p->phi_y, normals, alpha, p->include_alpha_norm, c->rec.p, c->yl.p, s), "pack");
   const int cfx = p->phi_x ? 1 : 0;
-  const int mode =
-      (p->include_alpha_norm || p->phi_x || p->phi_y) ? 1 : choose_mode(p->w, sigma2, volume, M, 0.0);
+  const int mode = (p->include_alpha_norm || p->phi_x || p->phi_y || p->precision == 1)
+                       ? 1
+                       : choose_mode(p->w, sigma2, volume, M, 0.0);
+  const int half = p->precision == 1 ? 1 : 0;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   LSG_CUDA(launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s), "prescale");
   if (mode == 1) {
-    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->ls_n.p, c->gam_n.p, s), "shift");
-    ++launches;
+    LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s), "shift");
+    launches += 2;
   }
-  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, c->ls_n.p, c->part.p, c->status, s), "estep");
+  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
   LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, per_n, s),
            "combine");

@@ -96,6 +96,19 @@ __device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
   return y;
 }
 
+// 2^-q for both halves through one packed f16x2 MUFU.EX2 (the mixed-precision
+// variant): -q is rounded to f16 (11-bit significand), the result widened back.
+__device__ __forceinline__ float2 ex2_neg_f16x2(float2 q) {
+  uint32_t h;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(-q.y), "f"(-q.x));  // upper = y, lower = x
+  asm("ex2.approx.f16x2 %0, %1;" : "=r"(h) : "r"(h));
+  float2 e;
+  asm("{ .reg .f16 lo, hi; mov.b32 {lo, hi}, %2; cvt.f32.f16 %0, lo; cvt.f32.f16 %1, hi; }"
+      : "=f"(e.x), "=f"(e.y)
+      : "r"(h));
+  return e;
+}
+
 struct Src {
   float2 z0, z1, z2;  // z^_n in both halves
   float2 ls;          // L_n in both halves (per-source shift mode)
@@ -112,9 +125,11 @@ struct Tgt {  // two consecutive targets, one per half
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // One source against two targets: 21 packed FP32 operations (22 + 1 with
-// per-source shifts) and 2 EX2.
-template <bool MAXS>
+// per-source shifts) and 2 EX2 (one packed f16x2 EX2 with MODE 2).
+// MODE: 0 uniform shift, 1 per-source shift, 2 per-source shift + f16x2 exponentials.
+template <int MODE>
 __device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g) {
+  constexpr bool MAXS = MODE == 1 || MODE == 2;
   const float2 r0 = __fadd2_rn(s.z0, g.ny0);
   const float2 r1 = __fadd2_rn(s.z1, g.ny1);
   const float2 r2 = __fadd2_rn(s.z2, g.ny2);
@@ -126,9 +141,18 @@ __device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g) 
   q = __ffma2_rn(r1, r1, q);
   q = __ffma2_rn(r2, r2, q);
   q = __ffma2_rn(v, v, q);
+  if (MODE == 3) {  // max pass (records hold lambda_m = -l_m): running min of q = c d - l_m
+    A.s0.x = fminf(A.s0.x, q.x);
+    A.s0.y = fminf(A.s0.y, q.y);
+    return;
+  }
   float2 e;
-  e.x = ex2_neg(q.x);
-  e.y = ex2_neg(q.y);
+  if (MODE == 2) {
+    e = ex2_neg_f16x2(q);
+  } else {
+    e.x = ex2_neg(q.x);
+    e.y = ex2_neg(q.y);
+  }
   A.s0 = __fadd2_rn(A.s0, e);
   A.b0 = __ffma2_rn(e, g.b0, A.b0);
   A.b1 = __ffma2_rn(e, g.b1, A.b1);
@@ -145,7 +169,7 @@ __device__ __forceinline__ void pair_update(Acc& A, const Src& s, const Tgt& g) 
 
 // All pairs of one tile: every thread walks the tile two targets at a time
 // (broadcast 64-bit shared loads of the 16 planes).
-template <int S, bool MAXS>
+template <int S, int MODE>
 __device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)[S], Acc (&acc)[S]) {
   const float2* T2 = reinterpret_cast<const float2*>(tile);
   constexpr int H = kTile / 2;
@@ -169,12 +193,17 @@ __device__ __forceinline__ void tile_compute(const float* tile, const Src (&src)
     g.b1 = T2[14 * H + q];
     g.b2 = T2[15 * H + q];
 #pragma unroll
-    for (int s = 0; s < S; ++s) pair_update<MAXS>(acc[s], src[s], g);
+    for (int s = 0; s < S; ++s) pair_update<MODE>(acc[s], src[s], g);
   }
 }
 
-template <bool MAXS>
+template <int MODE>
 __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc& a) {
+  constexpr bool MAXS = MODE == 1 || MODE == 2;
+  if (MODE == 3) {
+    dst[nl] = fminf(a.s0.x, a.s0.y);
+    return;
+  }
   dst[0 * SB + nl] = a.s0.x + a.s0.y;
   dst[1 * SB + nl] = a.b0.x + a.b0.y;
   dst[2 * SB + nl] = a.b1.x + a.b1.y;
@@ -199,12 +228,13 @@ struct Cursor {
   }
 };
 
-template <int S, bool MAXS>
+template <int S, int MODE>
 __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     estep_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
                  const float* __restrict__ ls_n, float* __restrict__ part, const int* __restrict__ tab,
                  const int* __restrict__ done_count, int* __restrict__ status, Geo g) {
   constexpr int SB = warps_for<S>() * 32 * S;
+  constexpr bool MAXS = MODE == 1 || MODE == 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tiles = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kStages * kTileBytes);
@@ -274,7 +304,8 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
       src[s2].z2 = dup(sqc * z2);
       src[s2].ls = dup(MAXS ? ls_n[n] : 0.f);
       const float2 zero = make_float2(0.f, 0.f);
-      acc[s2] = Acc{zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero, zero};
+      acc[s2] = Acc{MODE == 3 ? make_float2(INFINITY, INFINITY) : zero, zero, zero, zero, zero, zero, zero, zero,
+                    zero, zero, zero, zero};
     }
 
     for (; u < seg_end; ++u, ++i) {
@@ -282,7 +313,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
       const uint32_t parity = static_cast<uint32_t>(i / kStages) & 1u;
       const bool ok = mbar_wait(&full[stage], parity);
       if (!ok && lane == 0) atomicOr(status, kStatusTimeout);
-      tile_compute<S, MAXS>(tiles + stage * kTileFloats, src, acc);
+      tile_compute<S, MODE>(tiles + stage * kTileFloats, src, acc);
       if (__syncthreads_or(!ok)) {
         abort = true;
         break;
@@ -294,7 +325,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     if (abort) break;
     float* dst = part + static_cast<size_t>(first_slot + seg) * kMom * SB;
 #pragma unroll
-    for (int s2 = 0; s2 < S; ++s2) store_acc<MAXS>(dst, SB, warp * 32 * S + s2 * 32 + lane, acc[s2]);
+    for (int s2 = 0; s2 < S; ++s2) store_acc<MODE>(dst, SB, warp * 32 * S + s2 * 32 + lane, acc[s2]);
     ++seg;
   }
   if (abort && tid == 0) {
@@ -331,54 +362,37 @@ __global__ void __launch_bounds__(kTile)
 
 // ---------------------------------------------------------------------------
 // Per-source shift for the max-shift mode (used when w = 0, when a fixed shift
-// could overflow FP32, or when l_m varies): L_n = max(log2 gamma, max_m (l_m - c d_mn))
-// over the targets of the source's pair.  Planes 0-6 after prescale with
-// lambda_m = -l_m give l_m - c d = -(lambda_m + |r^|^2 + (a . r^)^2).
+// could overflow FP32, when l_m or w_n vary, and with f16 exponentials):
+// L_n = max(log2 gamma_n, max_m (l_m - c d_mn)) over the targets of the
+// source's pair.  The max itself comes from a pass of the E-step kernel in
+// MODE 3 (records prescaled with lambda_m = -l_m: l_m - c d = -q), which leaves
+// min_m q per source in every partial slot; this kernel takes the minimum over
+// the source block's slots and forms L_n and gamma'_n.
 // ---------------------------------------------------------------------------
 constexpr int kShiftThreads = 128;
 
 __global__ void __launch_bounds__(kShiftThreads)
-    shift_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
+    shift_kernel(const float4* __restrict__ xs, const float* __restrict__ part, const EmState* __restrict__ st,
                  const int* __restrict__ tab, const int* __restrict__ done_count, int cf_x,
                  float* __restrict__ ls_n, float* __restrict__ gam_n, Geo g) {
-  __shared__ __align__(16) float tile[7 * kTile];
   if (*done_count >= g.P) return;
   // every CTA covers kShiftThreads sources of one source block (SB is a multiple)
   const long long n = static_cast<long long>(blockIdx.x) * kShiftThreads + threadIdx.x;
   const int b = static_cast<int>(n / g.SB);
-  const int pair = tab[g.o_block_pair + b];
-  const EmState* sp = st + pair;
-  if (sp->done) return;  // uniform over the CTA
-  const float4 x = xs[n];
-  const float* R = sp->Rf;
-  const float sqc = sp->sqc;
-  const float z0 = sqc * fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, sp->tf[0])));
-  const float z1 = sqc * fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, sp->tf[1])));
-  const float z2 = sqc * fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, sp->tf[2])));
-  float best = INFINITY;  // min_m q_m
-  const int t0 = tab[g.o_tile_off + pair], t1 = tab[g.o_tile_off + pair + 1];
-  for (int t = t0; t < t1; ++t) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < 7 * kTile; e += kShiftThreads) tile[e] = rec[static_cast<size_t>(t) * kTileFloats + e];
-    __syncthreads();
-#pragma unroll 4
-    for (int j = 0; j < kTile; ++j) {
-      const float r0 = z0 + tile[0 * kTile + j];
-      const float r1 = z1 + tile[1 * kTile + j];
-      const float r2 = z2 + tile[2 * kTile + j];
-      const float v = fmaf(tile[4 * kTile + j], r0, fmaf(tile[5 * kTile + j], r1, tile[6 * kTile + j] * r2));
-      const float q = fmaf(v, v, fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, tile[3 * kTile + j]))));
-      best = fminf(best, q);
-    }
-  }
-  // padding sources (zero x) get finite values too; they are never read back
+  const int nl = static_cast<int>(n - static_cast<long long>(b) * g.SB);
+  const EmState* sp = st + tab[g.o_block_pair + b];
+  if (sp->done) return;
+  const int first = tab[g.o_block_slot + 2 * b];
+  const int count = tab[g.o_block_slot + 2 * b + 1];
+  float best = INFINITY;  // min_m q
+  for (int j = first; j < first + count; ++j) best = fminf(best, part[static_cast<size_t>(j) * kMom * g.SB + nl]);
   // log2 gamma_n (-inf without outlier term); per source with confidences: w_n = 1 - (1 - w0) phi_n
   float Lg = sp->L;
   if (cf_x) {
-    const float wn = 1.f - static_cast<float>(1.0 - sp->w0) * x.w;
+    const float wn = 1.f - static_cast<float>(1.0 - sp->w0) * xs[n].w;
     Lg = (wn > 0.f ? log2f(wn) - log2f(1.f - wn) : -INFINITY) + sp->Lb;
   }
-  const float L = fmaxf(-best, Lg);
+  const float L = fmaxf(-best, Lg);  // padding sources (zero x) get finite values too; never read back
   ls_n[n] = L;
   gam_n[n] = exp2f(Lg - L);  // gamma'_n = 2^(log2 gamma - L_n)
 }
@@ -554,10 +568,10 @@ __global__ void final_reduce_kernel(const double* __restrict__ rows, const int* 
   if (lane == 0) mom[static_cast<size_t>(pair) * kGlob + j] = v;
 }
 
-template <int S, bool MAXS>
+template <int S, int MODE>
 cudaError_t launch_estep_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
                            const float* ls_n, float* part, int* status, cudaStream_t s) {
-  estep_kernel<S, MAXS><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, ls_n, part, d.tab,
+  estep_kernel<S, MODE><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, ls_n, part, d.tab,
                                                                            d.done_count, status, p.g);
   return cudaGetLastError();
 }
@@ -567,11 +581,11 @@ int resident_ctas(int S) {
   const size_t smem = kStages * kTileBytes + kStages * sizeof(uint64_t);
   cudaError_t e = cudaSuccess;
   if (S == 4)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4, false>, warps_for<4>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<4, 0>, warps_for<4>() * 32, smem);
   else if (S == 2)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2, false>, warps_for<2>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<2, 0>, warps_for<2>() * 32, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1, false>, warps_for<1>() * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, estep_kernel<1, 0>, warps_for<1>() * 32, smem);
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     occ = 1;
@@ -710,19 +724,26 @@ BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long lon
 
 size_t estep_partial_floats(const Geo& g) { return static_cast<size_t>(g.total_slots) * kMom * g.SB; }
 
-cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode,
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode, int half,
                          const float* ls_n, float* part, int* status, cudaStream_t s) {
+  if (mode && half) {
+    switch (p.g.S) {
+      case 4: return launch_estep_t<4, 2>(p, d, xs, rec, ls_n, part, status, s);
+      case 2: return launch_estep_t<2, 2>(p, d, xs, rec, ls_n, part, status, s);
+      default: return launch_estep_t<1, 2>(p, d, xs, rec, ls_n, part, status, s);
+    }
+  }
   if (mode) {
     switch (p.g.S) {
-      case 4: return launch_estep_t<4, true>(p, d, xs, rec, ls_n, part, status, s);
-      case 2: return launch_estep_t<2, true>(p, d, xs, rec, ls_n, part, status, s);
-      default: return launch_estep_t<1, true>(p, d, xs, rec, ls_n, part, status, s);
+      case 4: return launch_estep_t<4, 1>(p, d, xs, rec, ls_n, part, status, s);
+      case 2: return launch_estep_t<2, 1>(p, d, xs, rec, ls_n, part, status, s);
+      default: return launch_estep_t<1, 1>(p, d, xs, rec, ls_n, part, status, s);
     }
   }
   switch (p.g.S) {
-    case 4: return launch_estep_t<4, false>(p, d, xs, rec, nullptr, part, status, s);
-    case 2: return launch_estep_t<2, false>(p, d, xs, rec, nullptr, part, status, s);
-    default: return launch_estep_t<1, false>(p, d, xs, rec, nullptr, part, status, s);
+    case 4: return launch_estep_t<4, 0>(p, d, xs, rec, nullptr, part, status, s);
+    case 2: return launch_estep_t<2, 0>(p, d, xs, rec, nullptr, part, status, s);
+    default: return launch_estep_t<1, 0>(p, d, xs, rec, nullptr, part, status, s);
   }
 }
 
@@ -733,9 +754,16 @@ cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, 
 }
 
 cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int cf_x,
-                         float* ls_n, float* gam_n, cudaStream_t s) {
+                         float* part, int* status, float* ls_n, float* gam_n, cudaStream_t s) {
+  cudaError_t e;
+  switch (p.g.S) {
+    case 4: e = launch_estep_t<4, 3>(p, d, xs, rec, nullptr, part, status, s); break;
+    case 2: e = launch_estep_t<2, 3>(p, d, xs, rec, nullptr, part, status, s); break;
+    default: e = launch_estep_t<1, 3>(p, d, xs, rec, nullptr, part, status, s);
+  }
+  if (e != cudaSuccess) return e;
   const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
-  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, rec, d.st, d.tab, d.done_count, cf_x,
+  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, part, d.st, d.tab, d.done_count, cf_x,
                                                                       ls_n, gam_n, p.g);
   return cudaGetLastError();
 }

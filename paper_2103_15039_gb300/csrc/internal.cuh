@@ -192,10 +192,13 @@ struct Dev {
 // Rewrite the sigma-dependent record planes 0-3 from yl for the current state.
 cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, int mode, float* rec,
                             cudaStream_t s);
-// mode 1 only: L_n and gamma'_n of every source (cf_x: per-source w_n from xs[n].w).
+// mode 1 only: L_n and gamma'_n of every source (cf_x: per-source w_n from xs[n].w): a
+// max pass of the E-step kernel (partials in part, overwritten by the E step after it)
+// and a per-source finalisation.
 cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int cf_x,
-                         float* ls_n, float* gam_n, cudaStream_t s);
-cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode,
+                         float* part, int* status, float* ls_n, float* gam_n, cudaStream_t s);
+// half (mode 1 only): exponentials as packed f16x2 (the mixed-precision variant).
+cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode, int half,
                          const float* ls_n, float* part, int* status, cudaStream_t s);
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
                            int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,

@@ -124,7 +124,7 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
                                               double* moments, float* per_n, void* stream) {
   if (!X || !Y || !normals || !alpha || !R || !t || !p || !moments) return LSGCPD_EINVAL;
   if (N < 1 || M < 1 || N > LSGCPD_NOALLOC_MAX_N || M > LSGCPD_NOALLOC_MAX_M) return LSGCPD_EINVAL;
-  if (!(p->w >= 0.0 && p->w < 1.0) || p->precision != 0) return LSGCPD_EINVAL;
+  if (!(p->w >= 0.0 && p->w < 1.0) || p->precision != 0) return LSGCPD_EINVAL;  // FP32 only
   if (!(sigma2 > 0.0) || !finite_d(sigma2) || !(volume > 0.0) || !finite_d(volume)) return LSGCPD_EINVAL;
   for (int i = 0; i < 9; ++i)
     if (!finite_d(R[i])) return LSGCPD_EINVAL;
@@ -170,8 +170,8 @@ extern "C" lsgcpd_status lsgcpd_estep_noalloc(const float* X, int64_t N, const f
     mode = (l_max - L + log2(static_cast<double>(M)) + 12.0 < 126.0) ? 0 : 1;
   }
   if (e == cudaSuccess) e = lsg::launch_prescale(plan, d, c.yl, mode, c.rec, s);
-  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, 0, c.ls, c.gam, s);
-  if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode, c.ls, c.part, c.status, s);
+  if (e == cudaSuccess && mode == 1) e = lsg::launch_shift(plan, d, c.xs, c.rec, 0, c.part, c.status, c.ls, c.gam, s);
+  if (e == cudaSuccess) e = lsg::launch_estep(plan, d, c.xs, c.rec, mode, 0, c.ls, c.part, c.status, s);
   if (e == cudaSuccess) e = lsg::launch_combine(plan, d, c.xs, c.part, mode, 0, c.ls, c.gam, c.rows, per_n, s);
   if (e == cudaSuccess) e = lsg::launch_final_reduce(plan, d, c.rows, c.mom, s);
   double mom[LSGCPD_MOMENTS];

@@ -88,13 +88,17 @@ def test_lidar_full_estep(lidar):
 
 
 def test_lidar_two_iteration_registration(lidar):
+    """Both E-step precisions against the oracle: FP32 at the task's bar, the
+    f16x2-exponential variant at its stated bound (1e-3 rad, 1e-4 of the diagonal)."""
     c, _, ctx = lidar
-    p = binding.default_params(max_iters=2)
-    got = ctx.register(c["X"], c["Y"], p)
     ref = oracle.register(c["X"], c["Y"], max_iters=2)
+    got = ctx.register(c["X"], c["Y"], binding.default_params(max_iters=2))
     assert oracle.rotation_error(got["R"], ref["R"]) < 1e-4
     assert np.linalg.norm(got["t"] - ref["t"]) / _diag(c["Y"]) < 1e-5
     assert got["sigma2"] == pytest.approx(ref["sigma2"], rel=1e-3)
+    half = ctx.register(c["X"], c["Y"], binding.default_params(max_iters=2, precision=1))
+    assert oracle.rotation_error(half["R"], ref["R"]) < 1e-3
+    assert np.linalg.norm(half["t"] - ref["t"]) / _diag(c["Y"]) < 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -147,3 +151,4 @@ def test_superquadric_registration_properties(superquadrics):
     R_gt, t_gt = c["R_gt"], c["t_gt"]
     assert oracle.rotation_error(got["R"], R_gt) < 1e-2
     assert np.linalg.norm(got["t"] - t_gt) / _diag(c["Y"]) < 1e-2
+
