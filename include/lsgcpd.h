@@ -207,9 +207,10 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const 
  * sources): fewer sources per thread waste less padding on small or uneven
  * pairs, more share each target tile among more sources.  With autotuning on,
  * the first lsgcpd_register / lsgcpd_register_batch call for a problem shape
- * (the list of N_i, M_i) whose E step has at most 1.5e10 pairs times one
- * E-step launch of each variant on the caller's data (after a warm-up launch)
- * and keeps the fastest; later calls with the same shape reuse the choice.
+ * (the list of N_i, M_i) whose E step has at most 1.5e10 pairs times three
+ * E-step launches of each variant on the caller's data (after a warm-up
+ * launch) and keeps the fastest, unless the fixed rule's choice is within 5%
+ * of it; later calls with the same shape reuse the choice.
  * With it off (or above the size limit) a fixed rule chooses.  The choice
  * changes only the FP32 summation order, so results within one context are
  * reproducible; two contexts can differ at FP32 rounding level.  The paper

@@ -584,10 +584,11 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   for (int i = 0; i < P; ++i) mode |= choose_mode(hs[i].w0, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
   const int cfx = in.phx ? 1 : 0;
   if (tune) {
-    // time one E-step launch (after a warm-up launch) for every source tile and keep the fastest;
-    // the target records do not depend on it, the source layout and the EM state are rebuilt
+    // time three back-to-back E-step launches (after a warm-up launch) for every source tile; the
+    // fastest wins unless the rule's own choice is within 5% of it (noise must not flip the plan);
+    // the target records do not depend on the tile, the source layout and the EM state are rebuilt
+    const int rule_S = plan.g.S;
     lsgcpd_ctx::Tuned rec{skey, plan.g.S, {0, 0, 0}};
-    double best = 1e300;
     for (const BatchPlan& pc : cands) {
       LSG_CUDA(upload_plan(c, pc, s), "plan");
       LSG_CUDA(init_state(pc), "init");
@@ -595,17 +596,24 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s), "shift");
       LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[0], s), "event");
-      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
+      for (int r = 0; r < 3; ++r)
+        LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[1], s), "event");
       LSG_CUDA(cudaEventSynchronize(c->tune_ev[1]), "sync");
-      const double ms = elapsed_ms(c->tune_ev[0], c->tune_ev[1]);
-      rec.ms[pc.g.S == 4 ? 0 : (pc.g.S == 2 ? 1 : 2)] = ms;
+      rec.ms[pc.g.S == 4 ? 0 : (pc.g.S == 2 ? 1 : 2)] = elapsed_ms(c->tune_ev[0], c->tune_ev[1]) / 3.0;
+      launches += (mode ? 5 : 3) + 2;
+    }
+    const auto slot = [](int S) { return S == 4 ? 0 : (S == 2 ? 1 : 2); };
+    double best = 1e300;
+    for (const BatchPlan& pc : cands) {
+      const double ms = rec.ms[slot(pc.g.S)];
       if (ms > 0 && ms < best) {
         best = ms;
         rec.S = pc.g.S;
       }
-      launches += (mode ? 5 : 3);
     }
+    const double rule_ms = rec.ms[slot(rule_S)];
+    if (rule_ms > 0 && rule_ms <= 1.05 * best) rec.S = rule_S;
     for (const BatchPlan& pc : cands)
       if (pc.g.S == rec.S) plan = pc;
     c->tuned.push_back(rec);
