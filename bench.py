@@ -298,6 +298,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     iters_run = got["iters"]
+    # device-time breakdown of the last timed step (CUDA events recorded by the library)
+    breakdown = {k: round(tm[k], 4) for k in ("ms_total", "ms_prep", "ms_estep", "ms_combine", "ms_mstep")}
 
     # --- end-to-end: pinned host inputs, copies inside the C call, result on the host ---
     e2e_s = []
@@ -340,7 +342,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4),
                    "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
-           "mode": got["mode"], "iters_run": iters_run, "e_step_plan": plan_obj(ctx)}
+           "mode": got["mode"], "iters_run": iters_run, "e_step_plan": plan_obj(ctx), "device_ms": breakdown}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, err = cpu_baseline(c, got, iters_run)
         out["cpu_baseline"] = cb

@@ -224,6 +224,15 @@ lsgcpd_status lsgcpd_set_autotune(lsgcpd_ctx* ctx, int enable);
  * sources per thread (0 where not measured).  Host memory. */
 lsgcpd_status lsgcpd_plan_info(const lsgcpd_ctx* ctx, int32_t info[4], double tune_ms[3]);
 
+/* Diagnostic of the failure path of the E step's copy pipeline (no
+ * counterpart in the paper): one kernel waits, with the same bounded wait the
+ * E step uses on its target-tile barriers, on a shared-memory barrier that
+ * nothing completes; after budget_cycles (1 .. 4e9 GPU clocks) it gives up and
+ * records the timeout.  Returns LSGCPD_ETIMEOUT when the wait ran out (the
+ * expected result) and leaves the context usable; LSGCPD_OK would mean the
+ * barrier completed.  Nothing faults, traps or hangs. */
+lsgcpd_status lsgcpd_selftest_timeout(lsgcpd_ctx* ctx, int64_t budget_cycles);
+
 /* Largest num_pairs of lsgcpd_register_batch. */
 #define LSGCPD_MAX_PAIRS 65535
 

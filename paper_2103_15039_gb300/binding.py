@@ -82,6 +82,8 @@ def lib():
         L.lsgcpd_register_batch.argtypes = [vp, C.c_int32, fp, C.POINTER(i64), fp, C.POINTER(i64),
                                             C.POINTER(Params), dp, dp, dp, C.POINTER(C.c_int32), dp, vp]
         L.lsgcpd_register_batch.restype = C.c_int
+        L.lsgcpd_selftest_timeout.argtypes = [vp, i64]
+        L.lsgcpd_selftest_timeout.restype = C.c_int
         L.lsgcpd_set_autotune.argtypes = [vp, C.c_int]
         L.lsgcpd_set_autotune.restype = C.c_int
         L.lsgcpd_plan_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
@@ -343,6 +345,11 @@ def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=N
     return out
 
 
+def lsgcpd_selftest_timeout(ctx, budget_cycles):
+    """Status code of the bounded-wait diagnostic (LSGCPD_ETIMEOUT = 4 is the expected result)."""
+    return int(lib().lsgcpd_selftest_timeout(ctx, int(budget_cycles)))
+
+
 def lsgcpd_set_autotune(ctx, enable):
     _check(ctx, lib().lsgcpd_set_autotune(ctx, 1 if enable else 0))
 
@@ -400,6 +407,9 @@ class Context:
 
     def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None, phi_x=None, phi_y=None):
         return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream, phi_x, phi_y)
+
+    def selftest_timeout(self, budget_cycles):
+        return lsgcpd_selftest_timeout(self.handle, budget_cycles)
 
     def set_autotune(self, enable):
         lsgcpd_set_autotune(self.handle, enable)

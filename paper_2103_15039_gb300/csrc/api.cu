@@ -837,6 +837,21 @@ lsgcpd_status lsgcpd_plan_info(const lsgcpd_ctx* c, int32_t info[4], double tune
   return LSGCPD_OK;
 }
 
+lsgcpd_status lsgcpd_selftest_timeout(lsgcpd_ctx* c, int64_t budget_cycles) {
+  if (!c) return LSGCPD_EINVAL;
+  c->err.clear();
+  if (budget_cycles < 1 || budget_cycles > 4000000000LL) return fail(c, LSGCPD_EINVAL, "budget out of range");
+  LSG_CUDA(cudaSetDevice(c->device), "device");
+  cudaStream_t s = c->stream;
+  int status = 0;
+  LSG_CUDA(cudaMemsetAsync(c->status, 0, sizeof(int), s), "memset");
+  LSG_CUDA(launch_wait_selftest(budget_cycles, c->status, s), "selftest");
+  LSG_CUDA(cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, s), "copy");
+  LSG_CUDA(cudaStreamSynchronize(s), "sync");
+  if (status & kStatusTimeout) return fail(c, LSGCPD_ETIMEOUT, "bounded wait gave up (expected)");
+  return LSGCPD_OK;
+}
+
 lsgcpd_status lsgcpd_last_timing(const lsgcpd_ctx* c, double out[8]) {
   if (!c || !out) return LSGCPD_EINVAL;
   for (int i = 0; i < 5; ++i) out[i] = c->last_timing[i];

@@ -74,8 +74,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
-// Wait for phase `parity` of the barrier; gives up after kWaitBudgetCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for phase `parity` of the barrier; gives up after `budget` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kWaitBudgetCycles) {
   const uint32_t a = smem_addr(bar);
   const long long t0 = clock64();
   while (true) {
@@ -86,7 +86,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kWaitBudgetCycles) return false;
+    if (clock64() - t0 > budget) return false;
   }
 }
 
@@ -595,7 +595,25 @@ int resident_ctas(int S) {
 
 int warps_of(int S) { return S >= 4 ? warps_for<4>() : (S == 2 ? warps_for<2>() : warps_for<1>()); }
 
+// Diagnostic: the bounded wait of the copy pipeline on a barrier that nothing
+// completes (no copy is issued); it must give up after `budget` cycles and
+// report the timeout in the status word, leaving the context usable.
+__global__ void wait_selftest_kernel(long long budget, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, budget)) atomicOr(status, kStatusTimeout);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(long long budget, int* status, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(budget, status);
+  return cudaGetLastError();
+}
 
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
                      int S_override) {

@@ -203,6 +203,8 @@ cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, con
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
                            int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
                            cudaStream_t s);
+// Diagnostic wait on a barrier nothing completes, bounded by `budget` cycles.
+cudaError_t launch_wait_selftest(long long budget, int* status, cudaStream_t s);
 // Sum each pair's combine rows (fixed order, FP64) into mom[P][kGlob]; one warp per moment.
 cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom,
                                 cudaStream_t s);
