@@ -529,7 +529,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_obj(c, seed, args.iters, ws),
+           "config": dict(config_obj(c, seed, args.iters, ws), e_step="fp64 (oracle)", m_step="fp64 (oracle)"),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"one EM iteration (E step + Newton M step) over {ns} of {N} sources "
                                       f"x {M} targets per step", "cpu": oracle.cpu_model()},
