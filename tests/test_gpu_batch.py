@@ -148,3 +148,23 @@ def test_full_size_batch_sampled_pairs(ctx):
         _close(got["R"][i], got["t"][i], ref, pairs[i]["Y"])
     finally:
         big.close()
+
+
+def test_thousands_of_tiny_pairs(ctx):
+    """3000 pairs of 10-40 points (grids with P in the thousands, many partial
+    tiles and blocks): sampled pairs against the oracle."""
+    rng = np.random.default_rng(91)
+    pairs = []
+    for i in range(3000):
+        n, m = int(rng.integers(10, 41)), int(rng.integers(10, 41))
+        Y = rng.normal(size=(m, 3)).astype(np.float32)
+        R0 = synth.random_rotation(rng, 0.3)
+        X = ((Y[rng.integers(0, m, n)] @ R0.T) + 0.02 * rng.normal(size=(n, 3))).astype(np.float32)
+        pairs.append(dict(X=X, Y=Y))
+    X, n_off, Y, m_off = _concat(pairs)
+    p = binding.default_params(max_iters=5, knn_k=5)
+    got = ctx.register_batch(X, n_off, Y, m_off, p)
+    assert np.all(np.isfinite(got["R"])) and np.all(got["iters"] == 5)
+    for i in (0, 1, 777, 2048, 2999):
+        ref = oracle.register(pairs[i]["X"], pairs[i]["Y"], max_iters=5, knn_k=5)
+        _close(got["R"][i], got["t"][i], ref, pairs[i]["Y"], rot_tol=1e-3, trans_tol=1e-4)
