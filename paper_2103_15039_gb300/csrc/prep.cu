@@ -272,10 +272,11 @@ __global__ void to_float4_kernel(const float* __restrict__ Y, long long M, float
 }
 
 // Insert (d, ci) into the sorted first k entries of (bd, bi); an equal distance
-// already present (lower index) stays first.  Fully unrolled over KMAX.
+// already present (lower index) stays first.  Fully unrolled over KMAX.  The new
+// threshold is min(k-th entry, cap) (cap bounds the k-th distance from above).
 template <int KMAX>
 __device__ __forceinline__ void knn_insert(float (&bd)[KMAX], int (&bi)[KMAX], float& thr, int k, float d,
-                                           int ci) {
+                                           int ci, float cap) {
 #pragma unroll
   for (int s = KMAX - 1; s >= 0; --s) {
     if (s < k) {
@@ -290,7 +291,26 @@ __device__ __forceinline__ void knn_insert(float (&bd)[KMAX], int (&bi)[KMAX], f
   }
 #pragma unroll
   for (int s = 0; s < KMAX; ++s)
-    if (s == k - 1) thr = bd[s];
+    if (s == k - 1) thr = fminf(bd[s], cap);
+}
+
+// An upper bound of the k-th nearest distance of query q: the largest distance
+// to k targets with indices next to q (scanned clouds keep neighbours close in
+// index, so the bound is tight there; it is valid for any order).  Returned just
+// above that distance, so that a strict comparison keeps every candidate with
+// d <= bound.  Same FP32 formula as the scan.
+__device__ __forceinline__ float knn_seed_bound(const float4* __restrict__ y, long long M, long long q, int k,
+                                                float4 p) {
+  long long s0 = q - k / 2;
+  if (s0 > M - k) s0 = M - k;
+  if (s0 < 0) s0 = 0;
+  float b = 0.f;
+  for (int j = 0; j < k; ++j) {
+    const float4 c = y[s0 + j];
+    const float dx = p.x + (-c.x), dy = p.y + (-c.y), dz = p.z + (-c.z);
+    b = fmaxf(b, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+  }
+  return b < INFINITY ? __uint_as_float(__float_as_uint(b) + 1u) : INFINITY;
 }
 
 // Two queries per thread (q and q + kKnnThreads), packed FP32x2 distances:
@@ -332,7 +352,11 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
     bd0[j] = bd1[j] = INFINITY;
     bi0[j] = bi1[j] = 0x7fffffff;
   }
-  float thr0 = INFINITY, thr1 = INFINITY;
+  // candidates above the seed bound can never enter the list: skipping them keeps the
+  // (divergent) insertions to the few near candidates
+  const float cap0 = v0 ? knn_seed_bound(y4 + m0, M, q0, k, p0) : INFINITY;
+  const float cap1 = v1 ? knn_seed_bound(y4 + m0, M, q1, k, p1) : INFINITY;
+  float thr0 = cap0, thr1 = cap1;
   for (long long base = c_lo; base < c_hi; base += kKnnTile) {
     const int cnt = static_cast<int>((c_hi - base) < kKnnTile ? (c_hi - base) : kKnnTile);
     __syncthreads();
@@ -349,8 +373,8 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
       const float2 dz = __fadd2_rn(pz, cz[j]);
       const float2 d = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
       const int ci = static_cast<int>(base + j);
-      if (d.x < thr0) knn_insert<KMAX>(bd0, bi0, thr0, k, d.x, ci);
-      if (d.y < thr1) knn_insert<KMAX>(bd1, bi1, thr1, k, d.y, ci);
+      if (d.x < thr0) knn_insert<KMAX>(bd0, bi0, thr0, k, d.x, ci, cap0);
+      if (d.y < thr1) knn_insert<KMAX>(bd1, bi1, thr1, k, d.y, ci, cap1);
     }
   }
   if (v0) {
