@@ -112,7 +112,8 @@ typedef struct {
   double t[3];
   double sigma2;
   int32_t iters;      /* EM iterations run */
-  int32_t mode;       /* 0: fixed outlier shift, 1: per-source max shift (w = 0 or extreme V) */
+  int32_t mode;       /* 0: uniform shift; 1: per-source shift (w = 0, extreme V, the Gaussian-constant
+                         option, confidences or f16 exponentials) */
   double ms_estep;    /* device time of the E-step kernels (only with timing enabled) */
   double ms_total;    /* device time of the whole call (only with timing enabled)     */
 } lsgcpd_result;
@@ -195,9 +196,13 @@ lsgcpd_status lsgcpd_mstep(lsgcpd_ctx* ctx, const double* moments, const double 
  * then p->max_iters EM iterations (E step, moment reduction, Newton M step,
  * sigma^2 update) captured once per problem shape in a CUDA graph and
  * replayed.  X and Y may be HOST or DEVICE pointers (detected per pointer);
- * host inputs are copied into the context.  out receives the result in the
- * caller's frame.  trace (host, max_iters x LSGCPD_TRACE_WIDTH doubles) may be
- * NULL.  Returns ENUMERIC if the posterior mass vanished (result = last pose). */
+ * host inputs are copied into the context.  The optional confidences
+ * (p->phi_x / p->phi_y, same memory as X / Y), confidence truncation
+ * (p->cf_threshold), outlier ratio (p->eta) and likelihood termination
+ * (p->nll_tol) apply as described at lsgcpd_params.  out receives the result
+ * in the caller's frame.  trace (host, max_iters x LSGCPD_TRACE_WIDTH doubles)
+ * may be NULL.  Returns ENUMERIC if the posterior mass vanished (result = last
+ * pose). */
 lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y, int64_t M,
                               const lsgcpd_params* p, lsgcpd_result* out, double* trace,
                               void* stream);
