@@ -178,19 +178,26 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
+def kernel_source_hash():
+    """sha256 over the sources that define the E-step kernel (its file and its copy pipeline)."""
+    h = hashlib.sha256()
+    for name in ("estep.cu", "pipeline.cuh"):
+        with open(os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def profile_traffic():
     """DRAM traffic per E-step launch from the committed ncu summary, if it was taken
     on the current kernel source (null otherwise)."""
     path = os.path.join(ROOT, "profiles", "estep_rgbd20k_traffic.json")
-    src = os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", "estep.cu")
     try:
         with open(path) as f:
             prof = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
+        h = kernel_source_hash()
     except OSError:
         return None
-    if prof.get("estep_cu_sha256") != h:
+    if prof.get("estep_source_sha256") != h:
         return None
     return prof.get("dram_bytes_per_launch")
 

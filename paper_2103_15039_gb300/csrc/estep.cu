@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "pipeline.cuh"
 
 namespace lsg {
 namespace {
@@ -48,48 +49,6 @@ template <int S>
 __host__ __device__ constexpr int warps_for() { return S >= 4 ? 8 : 4; }
 template <int S>
 __host__ __device__ constexpr int min_ctas_for() { return S >= 4 ? 1 : 3; }
-constexpr long long kWaitBudgetCycles = 4000000000LL;  // about 2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// Arm the barrier for `bytes` of transaction and start a bulk copy global -> shared.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Wait for phase `parity` of the barrier; gives up after `budget` cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kWaitBudgetCycles) {
-  const uint32_t a = smem_addr(bar);
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > budget) return false;
-  }
-}
-
 __device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
@@ -595,25 +554,7 @@ int resident_ctas(int S) {
 
 int warps_of(int S) { return S >= 4 ? warps_for<4>() : (S == 2 ? warps_for<2>() : warps_for<1>()); }
 
-// Diagnostic: the bounded wait of the copy pipeline on a barrier that nothing
-// completes (no copy is issued); it must give up after `budget` cycles and
-// report the timeout in the status word, leaving the context usable.
-__global__ void wait_selftest_kernel(long long budget, int* status) {
-  __shared__ uint64_t bar;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, budget)) atomicOr(status, kStatusTimeout);
-}
-
 }  // namespace
-
-cudaError_t launch_wait_selftest(long long budget, int* status, cudaStream_t s) {
-  wait_selftest_kernel<<<1, 32, 0, s>>>(budget, status);
-  return cudaGetLastError();
-}
 
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
                      int S_override) {
