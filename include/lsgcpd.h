@@ -214,7 +214,7 @@ lsgcpd_status lsgcpd_register(lsgcpd_ctx* ctx, const float* X, int64_t N, const 
  * the first lsgcpd_register / lsgcpd_register_batch call for a problem shape
  * (the list of N_i, M_i) whose E step has at most 1.5e10 pairs times three
  * E-step launches of each variant on the caller's data (after a warm-up
- * launch) and keeps the fastest, unless the fixed rule's choice is within 5%
+ * launch) and keeps the fastest, unless the fixed rule's choice is within 2%
  * of it; later calls with the same shape reuse the choice.
  * With it off (or above the size limit) a fixed rule chooses.  The choice
  * changes only the FP32 summation order, so results within one context are

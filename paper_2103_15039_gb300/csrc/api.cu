@@ -585,7 +585,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   const int cfx = in.phx ? 1 : 0;
   if (tune) {
     // time three back-to-back E-step launches (after a warm-up launch) for every source tile; the
-    // fastest wins unless the rule's own choice is within 5% of it (noise must not flip the plan);
+    // fastest wins unless the rule's own choice is within 2% of it (noise must not flip the plan);
     // the target records do not depend on the tile, the source layout and the EM state are rebuilt
     const int rule_S = plan.g.S;
     lsgcpd_ctx::Tuned rec{skey, plan.g.S, {0, 0, 0}};
@@ -613,7 +613,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       }
     }
     const double rule_ms = rec.ms[slot(rule_S)];
-    if (rule_ms > 0 && rule_ms <= 1.05 * best) rec.S = rule_S;
+    if (rule_ms > 0 && rule_ms <= 1.02 * best) rec.S = rule_S;
     for (const BatchPlan& pc : cands)
       if (pc.g.S == rec.S) plan = pc;
     c->tuned.push_back(rec);

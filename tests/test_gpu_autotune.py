@@ -31,8 +31,8 @@ def test_autotune_measures_every_tile_and_keeps_a_fastest():
         assert info["tuned"]
         ms = info["tune_ms"]
         assert all(v > 0 for v in ms.values())
-        # the fastest, or the fixed rule's choice when that is within 5% of the fastest
-        assert ms[info["sources_per_thread"]] <= 1.05 * min(ms.values())
+        # the fastest, or the fixed rule's choice when that is within 2% of the fastest
+        assert ms[info["sources_per_thread"]] <= 1.02 * min(ms.values())
         assert info["block"] == {4: 1024, 2: 256, 1: 128}[info["sources_per_thread"]]
         # the second call reuses the choice and reproduces the result bit for bit
         b = ctx.register(c["X"], c["Y"], p)
