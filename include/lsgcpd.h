@@ -172,7 +172,9 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* ctx, const float* Y, int64_t M, cons
  *           with r_mn = z_n - y_m and Lambda_m = I + alpha_m n_m n_m^T:
  *           [0] Pbar = sum_m P_mn, [1..3] h = sum_m P_mn Lambda_m r_mn,
  *           [4..9] W = sum_m P_mn alpha_m n_m n_m^T (00,01,02,11,12,22),
- *           [10] D = sum_m P_mn d_mn, d = r^T Lambda_m r, [11] Pout, [12..15] 0.
+ *           [10] D = sum_m P_mn d_mn, d = r^T Lambda_m r, [11] Pout,
+ *           [12] 1 / (S0_n + gamma'_n), the normaliser of the kernel's shifted
+ *           exponentials, [13] gamma'_n (shifted outlier term), [14..15] 0.
  * Uses p->w (0 allowed: no outlier term) as w0, p->include_alpha_norm and the
  * optional confidences p->phi_x / p->phi_y (DEVICE arrays of N / M floats;
  * Sec. 3.3: pi(m) = phi_m / sum phi, w_n = 1 - (1 - w0) phi_n; no truncation
@@ -182,6 +184,17 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* ctx, const float* X, int64_t N, const flo
                            const lsgcpd_params* p, const double R[9], const double t[3],
                            double sigma2, double volume, double* moments, float* per_n,
                            void* stream);
+
+/* The dense posteriors of one E step (Eq. (5)), for checking and debugging
+ * small problems: the E step of lsgcpd_estep (same arguments and rules), then
+ *   P  device, (M + 1) x N FP32, row-major: P[m][n] = P_mn for m < M (the
+ *      E step's own exponentials over its per-source normaliser), P[M][n] the
+ *      outlier posterior of source n.  Columns sum to 1 up to FP32 rounding.
+ * EINVAL if (M + 1) N exceeds 4e9. */
+lsgcpd_status lsgcpd_posteriors(lsgcpd_ctx* ctx, const float* X, int64_t N, const float* Y,
+                                const float* normals, const float* alpha, int64_t M,
+                                const lsgcpd_params* p, const double R[9], const double t[3],
+                                double sigma2, double volume, float* P, void* stream);
 
 /* M step from the global moments of one E step (Eqs. (11)-(13) and the
  * sigma^2 update): Newton on SE(3) with the posteriors fixed, starting at

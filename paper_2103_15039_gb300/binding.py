@@ -82,6 +82,9 @@ def lib():
         L.lsgcpd_register_batch.argtypes = [vp, C.c_int32, fp, C.POINTER(i64), fp, C.POINTER(i64),
                                             C.POINTER(Params), dp, dp, dp, C.POINTER(C.c_int32), dp, vp]
         L.lsgcpd_register_batch.restype = C.c_int
+        L.lsgcpd_posteriors.argtypes = [vp, fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
+                                        C.c_double, fp, vp]
+        L.lsgcpd_posteriors.restype = C.c_int
         L.lsgcpd_selftest_timeout.argtypes = [vp, i64]
         L.lsgcpd_selftest_timeout.restype = C.c_int
         L.lsgcpd_set_autotune.argtypes = [vp, C.c_int]
@@ -345,6 +348,27 @@ def lsgcpd_register_batch(ctx, X, n_off, Y, m_off, params, trace=False, stream=N
     return out
 
 
+def lsgcpd_posteriors(ctx, X, Y, normals, alpha, R, t, sigma2, volume, params, stream=None, phi_x=None,
+                      phi_y=None):
+    """Dense posteriors (M + 1) x N of one E step (outlier row last), as a CUDA tensor."""
+    import torch
+    N, M = X.shape[0], Y.shape[0]
+    _dev_ptr(X, "X", (N, 3))
+    _dev_ptr(Y, "Y", (M, 3))
+    _dev_ptr(normals, "normals", (M, 3))
+    _dev_ptr(alpha, "alpha", (M,))
+    Rd, td = _d(R, 9), _d(t, 3)
+    P = torch.empty((M + 1, N), dtype=torch.float32, device=X.device)
+    dpp = C.POINTER(C.c_double)
+    with _Confidences(params, phi_x, N, phi_y, M) as pp:
+        rc = lib().lsgcpd_posteriors(ctx, C.c_void_p(X.data_ptr()), N, C.c_void_p(Y.data_ptr()),
+                                     C.c_void_p(normals.data_ptr()), C.c_void_p(alpha.data_ptr()), M, C.byref(pp),
+                                     Rd.ctypes.data_as(dpp), td.ctypes.data_as(dpp), float(sigma2), float(volume),
+                                     C.c_void_p(P.data_ptr()), _stream(stream))
+    _check(ctx, rc)
+    return P
+
+
 def lsgcpd_selftest_timeout(ctx, budget_cycles):
     """Status code of the bounded-wait diagnostic (LSGCPD_ETIMEOUT = 4 is the expected result)."""
     return int(lib().lsgcpd_selftest_timeout(ctx, int(budget_cycles)))
@@ -407,6 +431,10 @@ class Context:
 
     def register_batch(self, X, n_off, Y, m_off, params, trace=False, stream=None, phi_x=None, phi_y=None):
         return lsgcpd_register_batch(self.handle, X, n_off, Y, m_off, params, trace, stream, phi_x, phi_y)
+
+    def posteriors(self, X, Y, normals, alpha, R, t, sigma2, volume, params, stream=None, phi_x=None, phi_y=None):
+        return lsgcpd_posteriors(self.handle, X, Y, normals, alpha, R, t, sigma2, volume, params, stream, phi_x,
+                                 phi_y)
 
     def selftest_timeout(self, budget_cycles):
         return lsgcpd_selftest_timeout(self.handle, budget_cycles)

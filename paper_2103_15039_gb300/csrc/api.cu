@@ -49,6 +49,7 @@ struct lsgcpd_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevBuf<float> X_in, Y_in, rec, part, knn_d, ls_n, gam_n;
   DevBuf<float> phx_in, phy_in, Xc, Yc, phxc, phyc;  // confidences; truncated clouds
+  DevBuf<float> pern_tmp;                             // per-source output for the dense posteriors
   DevBuf<int> cnt, coff;
   DevBuf<int> g_count, g_start, g_fill, g_cellof, g_scan;  // grid kNN
   DevBuf<float4> g_sorted;
@@ -793,7 +794,7 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  void* bufs2[] = {c->phx_in.p, c->phy_in.p, c->Xc.p,      c->Yc.p,       c->phxc.p,    c->phyc.p,   c->cnt.p,
+  void* bufs2[] = {c->pern_tmp.p, c->phx_in.p, c->phy_in.p, c->Xc.p,      c->Yc.p,       c->phxc.p,    c->phyc.p,   c->cnt.p,
                    c->coff.p,   c->toff.p,   c->g_count.p, c->g_start.p,  c->g_fill.p,  c->g_cellof.p,
                    c->g_scan.p, c->g_sorted.p, c->g_info.p};
   for (void* q : bufs2)
@@ -898,9 +899,15 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   return LSGCPD_OK;
 }
 
-lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float* Y, const float* normals,
-                           const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9], const double t[3],
-                           double sigma2, double volume, double* moments, float* per_n, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// One E step at (R, t, sigma2) with optional per-source output and, for small
+// problems, the dense posteriors (P: device, (M + 1) x N, outlier row last).
+lsgcpd_status estep_impl(lsgcpd_ctx* c, const float* X, int64_t N, const float* Y, const float* normals,
+                         const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9], const double t[3],
+                         double sigma2, double volume, double* moments, float* per_n, float* P, void* stream) {
   if (!c) return LSGCPD_EINVAL;
   c->err.clear();
   if (!X || !Y || !normals || !alpha || !R || !t) return fail(c, LSGCPD_EINVAL, "NULL input");
@@ -951,8 +958,17 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   }
   LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
-  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, per_n, s),
+  float* pn = per_n;
+  if (P && !pn) {
+    LSG_CUDA(ensure(c->pern_tmp, static_cast<size_t>(N) * LSGCPD_PER_N_WIDTH), "alloc");
+    pn = c->pern_tmp.p;
+  }
+  LSG_CUDA(launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, pn, s),
            "combine");
+  if (P) {
+    LSG_CUDA(launch_posteriors(c->xs.p, c->rec.p, c->st.p, c->ls_n.p, mode, half, pn, N, M, P, s), "posteriors");
+    ++launches;
+  }
   LSG_CUDA(launch_final_reduce(plan, d, c->rows.p, c->mom.p, s), "reduce");
   launches += 3;
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
@@ -979,6 +995,26 @@ lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float
   if (status & kStatusTimeout) return fail(c, LSGCPD_ETIMEOUT, "E-step tile wait timed out");
   if (moments) moments_to_raw(mom, hs.mu_x, moments);
   return LSGCPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsgcpd_status lsgcpd_estep(lsgcpd_ctx* c, const float* X, int64_t N, const float* Y, const float* normals,
+                           const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9], const double t[3],
+                           double sigma2, double volume, double* moments, float* per_n, void* stream) {
+  return estep_impl(c, X, N, Y, normals, alpha, M, p, R, t, sigma2, volume, moments, per_n, nullptr, stream);
+}
+
+lsgcpd_status lsgcpd_posteriors(lsgcpd_ctx* c, const float* X, int64_t N, const float* Y, const float* normals,
+                                const float* alpha, int64_t M, const lsgcpd_params* p, const double R[9],
+                                const double t[3], double sigma2, double volume, float* P, void* stream) {
+  if (!c) return LSGCPD_EINVAL;
+  if (!P) return fail(c, LSGCPD_EINVAL, "P is NULL");
+  if (N > 0 && M > 0 && static_cast<double>(N) * static_cast<double>(M + 1) > 4.0e9)
+    return fail(c, LSGCPD_EINVAL, "(M + 1) N above 4e9: the dense posteriors are for small problems");
+  return estep_impl(c, X, N, Y, normals, alpha, M, p, R, t, sigma2, volume, nullptr, nullptr, P, stream);
 }
 
 lsgcpd_status lsgcpd_mstep(lsgcpd_ctx* c, const double* moments, const double R[9], const double t[3],

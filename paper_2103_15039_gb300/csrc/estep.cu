@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kCombineThreads)
     o[0] = make_float4(Pb, h[0], h[1], h[2]);
     o[1] = make_float4(W00, W01, W02, W11);
     o[2] = make_float4(W12, W22, Dn, Pout);
-    o[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    o[3] = make_float4(inv, gp, 0.f, 0.f);  // the normaliser of the shifted exponentials, gamma'_n
   }
   const float A[6] = {Pb + W00, W01, W02, Pb + W11, W12, Pb + W22};
   const float xt[4] = {x0, x1, x2, valid ? 1.f : 0.f};
@@ -554,7 +554,49 @@ int resident_ctas(int S) {
 
 int warps_of(int S) { return S >= 4 ? warps_for<4>() : (S == 2 ? warps_for<2>() : warps_for<1>()); }
 
+// Dense posteriors of one pair (a debugging aid for small problems): thread per
+// source, P[m][n] = e_mn / (S0_n + gamma'_n) with e_mn recomputed exactly as the
+// E step computes it (same FP32 operations, same exponential), the outlier row
+// P[M][n] = Pout_n.  Needs the per-source output of the combine (per_n).
+__global__ void __launch_bounds__(128)
+    posterior_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const EmState* __restrict__ st,
+                     const float* __restrict__ ls_n, int mode, int half, const float* __restrict__ per_n,
+                     long long N, long long M, float* __restrict__ P) {
+  const long long n = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const float4 x = xs[n];
+  const float* R = st->Rf;
+  const float sqc = st->sqc;
+  const float z0 = sqc * fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, st->tf[0])));
+  const float z1 = sqc * fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, st->tf[1])));
+  const float z2 = sqc * fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, st->tf[2])));
+  const float Ln = mode ? ls_n[n] : 0.f;
+  const float inv = per_n[n * 16 + 12];
+  for (long long m = 0; m < M; ++m) {
+    const float* r = rec + (m / kTile) * kTileFloats + (m % kTile);
+    const float r0 = z0 + r[0 * kTile], r1 = z1 + r[1 * kTile], r2 = z2 + r[2 * kTile];
+    float v = r[4 * kTile] * r0;
+    v = fmaf(r[5 * kTile], r1, v);
+    v = fmaf(r[6 * kTile], r2, v);
+    float q = mode ? r[3 * kTile] + Ln : r[3 * kTile];
+    q = fmaf(r0, r0, q);
+    q = fmaf(r1, r1, q);
+    q = fmaf(r2, r2, q);
+    q = fmaf(v, v, q);
+    const float e = half ? ex2_neg_f16x2(make_float2(q, q)).x : ex2_neg(q);
+    P[m * N + n] = e * inv;
+  }
+  P[M * N + n] = per_n[n * 16 + 11];
+}
+
 }  // namespace
+
+cudaError_t launch_posteriors(const float4* xs, const float* rec, const EmState* st, const float* ls_n, int mode,
+                              int half, const float* per_n, long long N, long long M, float* P, cudaStream_t s) {
+  posterior_kernel<<<static_cast<unsigned>((N + 127) / 128), 128, 0, s>>>(xs, rec, st, ls_n, mode, half, per_n,
+                                                                           N, M, P);
+  return cudaGetLastError();
+}
 
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
                      int S_override) {

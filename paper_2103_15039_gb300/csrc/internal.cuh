@@ -203,6 +203,9 @@ cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, con
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
                            int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
                            cudaStream_t s);
+// Dense posteriors (M + 1) x N of a single pair after its E step (per_n from the combine).
+cudaError_t launch_posteriors(const float4* xs, const float* rec, const EmState* st, const float* ls_n, int mode,
+                              int half, const float* per_n, long long N, long long M, float* P, cudaStream_t s);
 // Diagnostic wait on a barrier nothing completes, bounded by `budget` cycles.
 cudaError_t launch_wait_selftest(long long budget, int* status, cudaStream_t s);
 // Sum each pair's combine rows (fixed order, FP64) into mom[P][kGlob]; one warp per moment.
