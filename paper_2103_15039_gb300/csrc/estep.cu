@@ -32,6 +32,8 @@
 //    grid of (SM count x resident CTAs); a CTA flushes its FP32 partial
 //    moments at block boundaries and every seg_cap tiles, so FP32 sums stay
 //    short; the combine adds the pieces (compensated) in a fixed order.
+// Kernel variants (MODE): 0 uniform shift; 1 per-source shift L_n; 2 per-source
+// shift with packed f16x2 exponentials; 3 the max pass that finds L_n.
 // No tensor cores: the contraction depth is 3, so the work is FP32-pipe bound.
 #include <math.h>
 
@@ -42,13 +44,14 @@ namespace lsg {
 namespace {
 
 constexpr int kStages = 4;
-// warps per CTA of the hot kernel: with 4 sources per thread (240 registers) one
+// warps per CTA of the hot kernel: with 4 sources per thread (190 registers) one
 // 8-warp CTA per SM shares each tile among 1024 sources; narrower variants run
 // several 4-warp CTAs per SM
 template <int S>
 __host__ __device__ constexpr int warps_for() { return S >= 4 ? 8 : 4; }
 template <int S>
 __host__ __device__ constexpr int min_ctas_for() { return S >= 4 ? 1 : 3; }
+
 __device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
@@ -241,6 +244,8 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
     if (seg_end > block_end) seg_end = block_end;
     if (seg_end > u1) seg_end = u1;
 
+    // a pair whose EM loop has finished keeps its tiles flowing through the ring but is not computed
+    const bool live = !sp->done;
     const float sqc = sp->sqc;
     float Rm[9], tv[3];
 #pragma unroll
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
       const uint32_t parity = static_cast<uint32_t>(i / kStages) & 1u;
       const bool ok = mbar_wait(&full[stage], parity);
       if (!ok && lane == 0) atomicOr(status, kStatusTimeout);
-      tile_compute<S, MODE>(tiles + stage * kTileFloats, src, acc);
+      if (live) tile_compute<S, MODE>(tiles + stage * kTileFloats, src, acc);
       if (__syncthreads_or(!ok)) {
         abort = true;
         break;

@@ -168,3 +168,17 @@ def test_thousands_of_tiny_pairs(ctx):
     for i in (0, 1, 777, 2048, 2999):
         ref = oracle.register(pairs[i]["X"], pairs[i]["Y"], max_iters=5, knn_k=5)
         _close(got["R"][i], got["t"][i], ref, pairs[i]["Y"], rot_tol=1e-3, trans_tol=1e-4)
+
+
+def test_batch_pairs_finish_at_their_own_iteration(ctx):
+    """With a motion tolerance pairs stop at different iterations; a finished pair is
+    no longer computed while the others continue, and each matches its own run."""
+    pairs = synth.batch_pairs(num_pairs=6, n_lo=200, n_hi=2500)
+    X, n_off, Y, m_off = _concat(pairs)
+    p = binding.default_params(max_iters=60, tol=1e-6)
+    got = ctx.register_batch(X, n_off, Y, m_off, p)
+    assert len(set(got["iters"].tolist())) > 1  # they really stop at different iterations
+    for i, c in enumerate(pairs):
+        one = ctx.register(c["X"], c["Y"], p)
+        assert abs(int(got["iters"][i]) - one["iters"]) <= 1
+        _close(got["R"][i], got["t"][i], one, c["Y"])
