@@ -12,13 +12,17 @@ pinned host inputs (H2D inside the call, result read back to the host).
 The roofline object reports the hot E-step kernel, timed live with CUDA events
 on the stream it is launched on, against the FP32-pipe peak (ALU bound).
 
+Other workloads (--workload): sphere1k (1,000 x 1,000 sphere + plane), lidar100k
+(two 64 x 1,563 LiDAR scans), superquadric500k (500,000 x 500,000 range scan),
+each one full registration per step like the default.
 With --workload batch256 a step is instead one batched registration of 256
 independent pairs with N, M log-uniform in [500, 20,000] (one launch per stage
 for the whole batch); the line then also carries the same 256 pairs registered
 one after another through lsgcpd_register (the plain per-pair form).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload rgbd20k|batch256]
+                       [--workload rgbd20k|sphere1k|lidar100k|superquadric500k|batch256]
+                       [--precision 0|1] [--iters I] [--no-cpu-baseline]
 Under torchrun every rank registers its own independent pair (weak scaling,
 no collective on the data path); rank 0 prints one JSON line.
 """
@@ -55,7 +59,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["rgbd20k", "batch256"], default="rgbd20k")
+    ap.add_argument("--workload", choices=["rgbd20k", "sphere1k", "lidar100k", "superquadric500k", "batch256"],
+                    default="rgbd20k")
     ap.add_argument("--precision", type=int, choices=[0, 1], default=0,
                     help="0: FP32 E step; 1: f16x2 exponentials (mixed precision)")
     return ap.parse_args()
@@ -90,10 +95,20 @@ def job_throughput(units_per_rank, ws, ms):
     return ws * units_per_rank / (ms / 1e3)
 
 
-def workload(rank):
+# single-pair workloads: name -> (seed offset, generator name, label)
+SINGLE = {
+    "sphere1k": (1, "sphere_plane_pair", "sphere_plane_1000x1000"),
+    "rgbd20k": (2, "rgbd_room_pair", "rgbd_room_20000x20000"),
+    "lidar100k": (3, "lidar_pair", "lidar_64x1563_100032x100032"),
+    "superquadric500k": (5, "superquadric_pair", "superquadrics_500000x500000"),
+}
+
+
+def workload(rank, name="rgbd20k"):
     from paper_2103_15039_gb300 import synth
-    seed = rank_seed(2, rank)
-    c = synth.rgbd_room_pair(seed=seed)
+    off, gen, _ = SINGLE[name]
+    seed = rank_seed(off, rank)
+    c = getattr(synth, gen)(seed=seed)
     return c, seed
 
 
@@ -110,10 +125,11 @@ def batch_workload(rank):
     return pairs, X, n_off, Y, m_off, seed
 
 
-def config_obj(c, seed, iters, n_gpus, precision=0):
-    return {"workload": "rgbd_room_20000x20000", "N": int(len(c["X"])), "M": int(len(c["Y"])),
+def config_obj(c, seed, iters, n_gpus, precision=0, name="rgbd20k"):
+    extra = {"overlap": round(float(c["overlap"]), 4)} if "overlap" in c else {}
+    return {"workload": SINGLE[name][2], "N": int(len(c["X"])), "M": int(len(c["Y"])),
             "em_iters": iters, "knn_k": 10, "w": 0.1, "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
-            "overlap": round(float(c["overlap"]), 4),
+            **extra,
             "e_step": "fp32 (packed f32x2) + ex2.approx" if precision == 0 else "fp32 residuals + f16x2 ex2.approx",
             "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus} (independent pairs per GPU)"}
@@ -273,7 +289,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    c, seed = workload(rank)
+    c, seed = workload(rank, args.workload)
     N, M = len(c["X"]), len(c["Y"])
     iters = args.iters
     ctx = binding.Context(local, N, M)
@@ -354,7 +370,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f16", "data": "synthetic",
-           "config": config_obj(c, seed, iters, ws, args.precision),
+           "config": config_obj(c, seed, iters, ws, args.precision, args.workload),
            "em_iters_per_s": ws * iters_run / (ms / 1e3),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
                    "d2h_bytes_per_step": xfer["d2h_bytes"], "ms_per_step": round(e2e_ms, 4),
@@ -517,7 +533,8 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    c, seed = workload(0)
+    name = args.workload if args.workload in SINGLE else "rgbd20k"
+    c, seed = workload(0, name)
     X, Y = c["X"], c["Y"]
     N, M = len(X), len(Y)
     pre = oracle.preprocess(Y, 10, 2.0, 0.2)
@@ -548,7 +565,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": dict(config_obj(c, seed, args.iters, ws), e_step="fp64 (oracle)", m_step="fp64 (oracle)"),
+           "config": dict(config_obj(c, seed, args.iters, ws, 0, name), e_step="fp64 (oracle)",
+                          m_step="fp64 (oracle)"),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"one EM iteration (E step + Newton M step) over {ns} of {N} sources "
                                       f"x {M} targets per step", "cpu": oracle.cpu_model()},
