@@ -40,7 +40,7 @@ constexpr int kMThreads = 128;
 // Power-series coefficients (-1)^k / (2k + o)! of sin(th)/th (o = 1), (1 - cos th)/th^2
 // (o = 2) and (th - sin th)/th^3 (o = 3) in powers of th^2, k = 0..8; the truncation
 // error is below 1e-19 for th^2 <= 1/4.
-__constant__ double c_exp_series[3][9] = {
+__device__ const double c_exp_series[3][9] = {
     {1.0, -0.16666666666666666, 0.008333333333333333, -0.0001984126984126984, 2.7557319223985893e-06, -2.505210838544172e-08, 1.6059043836821613e-10, -7.647163731819816e-13, 2.8114572543455206e-15},
     {0.5, -0.041666666666666664, 0.001388888888888889, -2.48015873015873e-05, 2.755731922398589e-07, -2.08767569878681e-09, 1.1470745597729725e-11, -4.779477332387385e-14, 1.5619206968586225e-16},
     {0.16666666666666666, -0.008333333333333333, 0.0001984126984126984, -2.7557319223985893e-06, 2.505210838544172e-08, -1.6059043836821613e-10, 7.647163731819816e-13, -2.8114572543455206e-15, 8.22063524662433e-18}};
@@ -132,7 +132,7 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
   return h;
 }
 
-__constant__ HessTab c_hess = make_hess_tab();
+__device__ const HessTab c_hess = make_hess_tab();
 
 struct Shared {
   double SD, NP;
@@ -193,8 +193,9 @@ __device__ void load_model(Shared& s, const double* mom) {
   {
     const int* src = reinterpret_cast<const int*>(&c_hess);
     int* dst = reinterpret_cast<int*>(&s.hess);
-    for (int i = tid; i < static_cast<int>(sizeof(HessTab) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-    if (tid < 27) s.series[tid / 9][tid % 9] = c_exp_series[tid / 9][tid % 9];
+    // global (not constant) memory: every lane reads a different word, so the loads coalesce
+    for (int i = tid; i < static_cast<int>(sizeof(HessTab) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(src + i);
+    if (tid < 27) s.series[tid / 9][tid % 9] = __ldg(&c_exp_series[tid / 9][tid % 9]);
   }
   if (tid == 0) {
     s.NP = mom[0];
@@ -266,6 +267,13 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     for (int l = 0; l < 4; ++l)
 #pragma unroll
       for (int j = 0; j < 3; ++j) gidx[3 * l + j] = pair_q(k, l) * 6 + sym_p(i, j);
+  }
+  // the model does not change during the loop: lanes < 12 keep their 12 entries in registers
+  double ga[12];
+  {
+    const double* Af = &s.A[0][0];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) ga[j] = tid < 12 ? Af[gidx[j]] : 0.0;
   }
   if (tid < 12) s.M1[tid] = s.H1[tid];
   if (tid == 0) {
@@ -410,13 +418,12 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       if (tid < 32) {  // G D and dQ = 2 <M1, D> + <D, G D>
         double dq = 0.0;
         if (tid < 12) {
-          const double* Af = &s.A[0][0];
           double gl[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {  // four independent chains of three
-            gl[l] = Af[gidx[3 * l]] * s.dl[l];
-            gl[l] = fma(Af[gidx[3 * l + 1]], s.dl[4 + l], gl[l]);
-            gl[l] = fma(Af[gidx[3 * l + 2]], s.dl[8 + l], gl[l]);
+            gl[l] = ga[3 * l] * s.dl[l];
+            gl[l] = fma(ga[3 * l + 1], s.dl[4 + l], gl[l]);
+            gl[l] = fma(ga[3 * l + 2], s.dl[8 + l], gl[l]);
           }
           const double g = (gl[0] + gl[1]) + (gl[2] + gl[3]);
           s.Gd[tid] = g;
