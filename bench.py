@@ -22,7 +22,7 @@ one after another through lsgcpd_register (the plain per-pair form).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload rgbd20k|sphere1k|lidar100k|superquadric500k|batch256]
-                       [--precision 0|1] [--iters I] [--no-cpu-baseline]
+                       [--precision 0|1|2] [--iters I] [--no-cpu-baseline]
 Under torchrun every rank registers its own independent pair (weak scaling,
 no collective on the data path); rank 0 prints one JSON line.
 """
@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["rgbd20k", "sphere1k", "lidar100k", "superquadric500k", "batch256"],
                     default="rgbd20k")
-    ap.add_argument("--precision", type=int, choices=[0, 1], default=0,
-                    help="0: FP32 E step; 1: f16x2 exponentials (mixed precision)")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
+                    help="0: FP32 E step; 1: f16x2 exponentials (mixed precision); "
+                         "2: TF32 exponentials with the moment sums on the tensor cores")
     return ap.parse_args()
 
 
@@ -125,12 +126,19 @@ def batch_workload(rank):
     return pairs, X, n_off, Y, m_off, seed
 
 
+E_STEP_DESC = {0: "fp32 (packed f32x2) + ex2.approx",
+               1: "fp32 residuals + f16x2 ex2.approx",
+               2: "fp32 residuals + ex2.approx, exponentials truncated to tf32, moment sums on tcgen05 "
+                  "(tf32 x hi/lo features, f32 accumulation in tensor memory)"}
+DTYPE = {0: "f32", 1: "f32+f16", 2: "f32+tf32"}
+
+
 def config_obj(c, seed, iters, n_gpus, precision=0, name="rgbd20k"):
     extra = {"overlap": round(float(c["overlap"]), 4)} if "overlap" in c else {}
     return {"workload": SINGLE[name][2], "N": int(len(c["X"])), "M": int(len(c["Y"])),
             "em_iters": iters, "knn_k": 10, "w": 0.1, "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
             **extra,
-            "e_step": "fp32 (packed f32x2) + ex2.approx" if precision == 0 else "fp32 residuals + f16x2 ex2.approx",
+            "e_step": E_STEP_DESC[precision],
             "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus} (independent pairs per GPU)"}
 
@@ -369,7 +377,7 @@ def run_ours(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f16", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
            "config": config_obj(c, seed, iters, ws, args.precision, args.workload),
            "em_iters_per_s": ws * iters_run / (ms / 1e3),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],
@@ -489,7 +497,7 @@ def run_batch(args):
             "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32" if args.precision == 0 else "f32+f16", "data": "synthetic",
+           "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
            "config": {"workload": "batch_256_pairs_500_20000", "pairs": P, "sum_N": int(Ns.sum()),
                       "sum_M": int(Ms.sum()), "sum_NM": int(nm.sum()), "em_iters": iters, "knn_k": 10, "w": 0.1,
                       "alpha_max": 2.0, "lambda": 0.2, "seed": seed,

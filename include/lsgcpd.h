@@ -81,7 +81,11 @@ typedef struct {
   int32_t include_alpha_norm; /* 0: Eq. (9) as printed; 1: component constant with sqrt(1+alpha) */
   int32_t newton_max; /* inner Newton steps per M step (default 20)                       */
   int32_t precision;  /* 0: FP32 E step; 1: FP32 residuals with packed f16x2 exponentials
-                         (per-source shifts; posteriors to ~1e-3 relative) */
+                         (per-source shifts; posteriors to ~1e-3 relative); 2: FP32 residuals and
+                         exponentials, exponentials truncated to TF32 and the moment sums of
+                         Eq. (9) (a product over the targets) on the tensor cores (tcgen05, TF32
+                         operands with hi + lo features, FP32 accumulation; per-source moments to
+                         ~2e-3 relative; lsgcpd_posteriors stays FP32) */
   int32_t knn_method; /* neighbour search: 0 auto (uniform grid above 50,000 targets in the largest
                          pair, brute force below), 1 brute force, 2 uniform grid; all give the same lists */
   /* Outlier weight from the outlier ratio (Sec. 3.2): eta in (0, 1) sets

@@ -32,9 +32,9 @@ struct DevBuf {
 struct GraphKey {
   std::vector<long long> sizes;
   std::vector<unsigned char> params;
-  int iters = -1, mode = -1, half = -1, S = -1, timing = -1, trace = -1;
+  int iters = -1, mode = -1, prec = -1, S = -1, timing = -1, trace = -1;
   bool operator==(const GraphKey& o) const {
-    return sizes == o.sizes && params == o.params && iters == o.iters && mode == o.mode && half == o.half &&
+    return sizes == o.sizes && params == o.params && iters == o.iters && mode == o.mode && prec == o.prec &&
            S == o.S && timing == o.timing && trace == o.trace;
   }
 };
@@ -48,6 +48,7 @@ struct lsgcpd_ctx {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   DevBuf<float> X_in, Y_in, rec, part, knn_d, ls_n, gam_n;
+  DevBuf<float> feat;  // feature tiles of the tensor-core E step (precision 2)
   DevBuf<float> phx_in, phy_in, Xc, Yc, phxc, phyc;  // confidences; truncated clouds
   DevBuf<float> pern_tmp;                             // per-source output for the dense posteriors
   DevBuf<int> cnt, coff;
@@ -136,8 +137,9 @@ lsgcpd_status check_params(lsgcpd_ctx* c, const lsgcpd_params* p) {
     return fail(c, LSGCPD_EINVAL, "sigma2_floor_rel must be >= 0");
   if (p->max_iters < 0 || p->max_iters > 100000) return fail(c, LSGCPD_EINVAL, "max_iters out of range");
   if (p->newton_max < 1 || p->newton_max > 1000) return fail(c, LSGCPD_EINVAL, "newton_max out of range");
-  if (p->precision != 0 && p->precision != 1)
-    return fail(c, LSGCPD_EINVAL, "precision must be 0 (FP32) or 1 (f16x2 exponentials)");
+  if (p->precision < 0 || p->precision > 2)
+    return fail(c, LSGCPD_EINVAL,
+                "precision must be 0 (FP32), 1 (f16x2 exponentials) or 2 (tensor-core moments)");
   if (!(p->eta >= 0.0 && p->eta < 1.0)) return fail(c, LSGCPD_EINVAL, "eta must be in [0, 1)");
   if (!is_finite_d(p->cf_threshold) || p->cf_threshold < 0.0)
     return fail(c, LSGCPD_EINVAL, "cf_threshold must be finite and >= 0");
@@ -235,7 +237,7 @@ cudaError_t leave(lsgcpd_ctx* c, void* stream) {
 
 // Scratch for a plan; k = 0 skips the neighbour buffers.  A buffer that has to
 // grow moves, so the captured graph (which holds the old addresses) is dropped.
-lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool host_inputs) {
+lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool host_inputs, bool tc = false) {
   const Geo& g = p.g;
   const size_t n_pad = static_cast<size_t>(g.B) * g.SB;
   const size_t m_pad = static_cast<size_t>(g.T) * kTile;
@@ -249,6 +251,7 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
   };
   grow(c->xs, n_pad);
   grow(c->rec, m_pad * kPlanes);
+  if (tc) grow(c->feat, tc_feature_floats(g));
   grow(c->yl, m_pad);
   grow(c->part, estep_partial_floats(g));
   grow(c->rows, static_cast<size_t>(g.combine_ctas) * kGlob);
@@ -284,6 +287,13 @@ lsgcpd_status reserve(lsgcpd_ctx* c, const BatchPlan& p, int k, int iters, bool 
 }
 
 Dev dev_of(lsgcpd_ctx* c) { return Dev{c->tab.p, c->off64.p, c->st.p, c->done_count}; }
+
+// One E-step launch for the precision: 0 FP32, 1 f16x2 exponentials, 2 moments on the tensor cores.
+cudaError_t estep_launch(lsgcpd_ctx* c, const BatchPlan& plan, const Dev& d, int mode, int prec, cudaStream_t s) {
+  if (prec == 2)
+    return launch_estep_tc(plan, d, c->xs.p, c->rec.p, c->feat.p, mode, c->ls_n.p, c->part.p, c->status, s);
+  return launch_estep(plan, d, c->xs.p, c->rec.p, mode, prec == 1 ? 1 : 0, c->ls_n.p, c->part.p, c->status, s);
+}
 
 // k nearest targets of every target (needs the pair AABBs from launch_init for the grid).
 cudaError_t run_knn(lsgcpd_ctx* c, const BatchPlan& plan, const Dev& d, const float* Y, int k, int method,
@@ -538,12 +548,14 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       if (t.sizes == skey) hit = &t;
   double pairs = 0;
   for (int i = 0; i < P; ++i) pairs += static_cast<double>(N[i]) * static_cast<double>(M[i]);
-  const bool tune = c->autotune && iters > 0 && !hit && pairs <= kTuneMaxPairs;
-  BatchPlan plan = plan_batch(N, M, c->num_sms, hit ? hit->S : 0);
+  // the tensor-core E step has one source tile (4 sources per thread): nothing to tune
+  const bool tc = p->precision == 2;
+  const bool tune = c->autotune && iters > 0 && !hit && pairs <= kTuneMaxPairs && !tc;
+  BatchPlan plan = plan_batch(N, M, c->num_sms, tc ? 4 : (hit ? hit->S : 0));
   std::vector<BatchPlan> cands;
   if (tune)
     for (int S : {4, 2, 1}) cands.push_back(S == plan.g.S ? plan : plan_batch(N, M, c->num_sms, S));
-  rs = reserve(c, plan, k, iters, false);
+  rs = reserve(c, plan, k, iters, false, tc);
   for (size_t i = 0; i < cands.size() && rs == LSGCPD_OK; ++i) rs = reserve(c, cands[i], k, iters, false);
   if (rs != LSGCPD_OK) return rs;
   const Dev d = dev_of(c);
@@ -567,6 +579,10 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     LSG_CUDA(launch_eta(plan, d, c->yl.p, p->eta, s), "eta");
     ++launches;
   }
+  if (tc) {
+    LSG_CUDA(launch_features(plan, c->rec.p, c->yl.p, c->feat.p, s), "features");
+    ++launches;
+  }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
   std::vector<EmState> hs(P);
   int status = 0;
@@ -581,7 +597,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
   // uniform (the uniform-shift moments assume one l) and w_n is uniform
   const double l_extra = p->include_alpha_norm ? 0.5 * log2(1.0 + p->alpha_max) : 0.0;
   int mode = (p->include_alpha_norm || in.phx || in.phy || p->precision == 1) ? 1 : 0;
-  const int half = p->precision == 1 ? 1 : 0;
+  const int prec = p->precision;
   for (int i = 0; i < P; ++i) mode |= choose_mode(hs[i].w0, hs[i].sigma2_floor, hs[i].V, M[i], l_extra);
   const int cfx = in.phx ? 1 : 0;
   if (tune) {
@@ -595,10 +611,9 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       LSG_CUDA(init_state(pc), "init");
       LSG_CUDA(launch_prescale(pc, d, c->yl.p, mode, c->rec.p, s), "prescale");
       if (mode) LSG_CUDA(launch_shift(pc, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s), "shift");
-      LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
+      LSG_CUDA(estep_launch(c, pc, d, mode, prec, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[0], s), "event");
-      for (int r = 0; r < 3; ++r)
-        LSG_CUDA(launch_estep(pc, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
+      for (int r = 0; r < 3; ++r) LSG_CUDA(estep_launch(c, pc, d, mode, prec, s), "estep");
       LSG_CUDA(cudaEventRecord(c->tune_ev[1], s), "event");
       LSG_CUDA(cudaEventSynchronize(c->tune_ev[1]), "sync");
       rec.ms[pc.g.S == 4 ? 0 : (pc.g.S == 2 ? 1 : 2)] = elapsed_ms(c->tune_ev[0], c->tune_ev[1]) / 3.0;
@@ -636,7 +651,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
                       reinterpret_cast<const unsigned char*>(&dp) + sizeof(dp));
     key.iters = iters;
     key.mode = mode;
-    key.half = half;
+    key.prec = prec;
     key.S = g.S;
     key.timing = c->timing;
     key.trace = trace ? 1 : 0;
@@ -653,7 +668,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         if (ce == cudaSuccess) ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
         if (ce == cudaSuccess && mode == 1)
           ce = launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s);
-        if (ce == cudaSuccess) ce = launch_estep(plan, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s);
+        if (ce == cudaSuccess) ce = estep_launch(c, plan, d, mode, prec, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 1], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
@@ -796,7 +811,7 @@ void lsgcpd_destroy(lsgcpd_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   void* bufs2[] = {c->pern_tmp.p, c->phx_in.p, c->phy_in.p, c->Xc.p,      c->Yc.p,       c->phxc.p,    c->phyc.p,   c->cnt.p,
                    c->coff.p,   c->toff.p,   c->g_count.p, c->g_start.p,  c->g_fill.p,  c->g_cellof.p,
-                   c->g_scan.p, c->g_sorted.p, c->g_info.p};
+                   c->g_scan.p, c->g_sorted.p, c->g_info.p, c->feat.p};
   for (void* q : bufs2)
     if (q) cudaFree(q);
   void* bufs[] = {c->X_in.p, c->Y_in.p,    c->rec.p, c->part.p,  c->knn_d.p, c->ls_n.p, c->gam_n.p,
@@ -921,8 +936,9 @@ lsgcpd_status estep_impl(lsgcpd_ctx* c, const float* X, int64_t N, const float* 
   for (int i = 0; i < 3; ++i)
     if (!is_finite_d(t[i])) return fail(c, LSGCPD_EINVAL, "t must be finite");
   LSG_CUDA(enter(c, stream), "stream");
-  const BatchPlan plan = plan_batch({N}, {M}, c->num_sms, 0);
-  lsgcpd_status rs = reserve(c, plan, 0, 1, false);
+  const bool tc = p->precision == 2;
+  const BatchPlan plan = plan_batch({N}, {M}, c->num_sms, tc ? 4 : 0);
+  lsgcpd_status rs = reserve(c, plan, 0, 1, false, tc);
   if (rs != LSGCPD_OK) return rs;
   cudaStream_t s = c->stream;
   const Dev d = dev_of(c);
@@ -945,18 +961,22 @@ lsgcpd_status estep_impl(lsgcpd_ctx* c, const float* X, int64_t N, const float* 
   LSG_CUDA(launch_init(plan, d, X, Y, p->phi_x, p->phi_y, dp, false, c->red.p, c->xs.p, s), "center");
   LSG_CUDA(launch_estep_constants(c->st.p, sigma2, p->w, volume, R, t, s), "constants");
   LSG_CUDA(launch_pack(plan, d, Y, p->phi_y, normals, alpha, p->include_alpha_norm, c->rec.p, c->yl.p, s), "pack");
+  if (tc) {
+    LSG_CUDA(launch_features(plan, c->rec.p, c->yl.p, c->feat.p, s), "features");
+    ++launches;
+  }
   const int cfx = p->phi_x ? 1 : 0;
   const int mode = (p->include_alpha_norm || p->phi_x || p->phi_y || p->precision == 1)
                        ? 1
                        : choose_mode(p->w, sigma2, volume, M, 0.0);
-  const int half = p->precision == 1 ? 1 : 0;
+  const int half = p->precision == 1 ? 1 : 0;  // the dense posteriors of precision 2 are FP32
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   LSG_CUDA(launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s), "prescale");
   if (mode == 1) {
     LSG_CUDA(launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s), "shift");
     launches += 2;
   }
-  LSG_CUDA(launch_estep(plan, d, c->xs.p, c->rec.p, mode, half, c->ls_n.p, c->part.p, c->status, s), "estep");
+  LSG_CUDA(estep_launch(c, plan, d, mode, p->precision, s), "estep");
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_prep, s), "event");
   float* pn = per_n;
   if (P && !pn) {

@@ -200,6 +200,15 @@ cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, con
 // half (mode 1 only): exponentials as packed f16x2 (the mixed-precision variant).
 cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int mode, int half,
                          const float* ls_n, float* part, int* status, cudaStream_t s);
+// ----- E step with the moment contraction on tcgen05 (estep_tc.cu) -----------------
+// Feature tiles (the B operand: b, a a^T, lambda split hi + lo in TF32) of every
+// record slot, built once from the static record planes; floats for a plan.
+size_t tc_feature_floats(const Geo& g);
+cudaError_t launch_features(const BatchPlan& p, const float* rec, const float4* yl, float* feat, cudaStream_t s);
+// Same partial moments as launch_estep with 4 sources per thread (p.g.SB must be
+// 1024), exponentials truncated to TF32; mode 0 or 1 (after launch_shift).
+cudaError_t launch_estep_tc(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, const float* feat,
+                            int mode, const float* ls_n, float* part, int* status, cudaStream_t s);
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
                            int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
                            cudaStream_t s);
