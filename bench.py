@@ -45,6 +45,7 @@ sys.path.insert(0, ROOT)
 METRIC = "E-step pair-evals/sec & EM iters/sec at 1 GB300; % FP32/SFU roofline; rot err vs FP64"
 UNIT = "pair-evals/s"
 FLOPS_PER_PAIR = 27  # FP32-pipe operations per (source, target) pair, the fixed algorithmic count
+TC_FP32_OPS_PER_PAIR = 11  # what stays on the FP32 pipe when the moment sums run on the tensor cores
 EX2_PER_PAIR = 1
 SM_MAX_MHZ_NOMINAL = 2070.0
 FP32_LANES_PER_SM = 128
@@ -61,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["rgbd20k", "sphere1k", "lidar100k", "superquadric500k", "batch256"],
                     default="rgbd20k")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the second measurement of the same workload with precision 2")
     ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
                     help="0: FP32 E step; 1: f16x2 exponentials (mixed precision); "
                          "2: TF32 exponentials with the moment sums on the tensor cores")
@@ -202,23 +205,26 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
-def kernel_source_hash():
+def kernel_source_hash(precision=0):
     """sha256 over the sources that define the E-step kernel (its file and its copy pipeline)."""
     h = hashlib.sha256()
-    for name in ("estep.cu", "pipeline.cuh"):
+    for name in (("estep_tc.cu",) if precision == 2 else ("estep.cu",)) + ("pipeline.cuh",):
         with open(os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def profile_traffic():
+def profile_traffic(precision=0, workload="rgbd20k"):
     """DRAM traffic per E-step launch from the committed ncu summary, if it was taken
-    on the current kernel source (null otherwise)."""
-    path = os.path.join(ROOT, "profiles", "estep_rgbd20k_traffic.json")
+    on the current kernel source and on this workload (null otherwise)."""
+    if workload != "rgbd20k":
+        return None
+    name = "estep_tc_rgbd20k_traffic.json" if precision == 2 else "estep_rgbd20k_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             prof = json.load(f)
-        h = kernel_source_hash()
+        h = kernel_source_hash(precision)
     except OSError:
         return None
     if prof.get("estep_source_sha256") != h:
@@ -272,10 +278,7 @@ def cpu_baseline(c, got, iters, budget_s=40.0):
         out["value"] = ref["iters"] * N * M / dt
         out["sample"] = f"full registration: kNN + geometry + {ref['iters']} EM iterations of the same pair"
         out["seconds"] = round(dt, 2)
-        err = {"rot_err_rad": oracle.rotation_error(got["R"], ref["R"]),
-               "trans_err_rel_diag": float(np.linalg.norm(got["t"] - ref["t"]) / diag),
-               "sigma2_rel": abs(got["sigma2"] - ref["sigma2"]) / ref["sigma2"]}
-        return out, err
+        return out, dict(ref, diag=diag)
     ns = max(1, min(N, int(20.0 * rate / M)))
     t0 = time.perf_counter()
     oracle.estep(X[:ns], Y, pre["normals"], pre["alpha"], np.eye(3), np.zeros(3), 0.05, 0.1, V)
@@ -284,6 +287,38 @@ def cpu_baseline(c, got, iters, budget_s=40.0):
     out["sample"] = f"one E step over {ns} of {N} sources x {M} targets"
     out["seconds"] = round(dt, 2)
     return out, None
+
+
+def oracle_rot(Ra, Rb):
+    import oracle
+    return oracle.rotation_error(Ra, Rb)
+
+
+def errors_vs(got, ref, diag):
+    """Rotation / translation / sigma^2 error of a GPU result against a reference result."""
+    import numpy as np
+
+    import oracle
+    return {"rot_err_rad": oracle.rotation_error(got["R"], ref["R"]),
+            "trans_err_rel_diag": float(np.linalg.norm(got["t"] - ref["t"]) / diag),
+            "sigma2_rel": abs(got["sigma2"] - ref["sigma2"]) / ref["sigma2"]}
+
+
+def time_registrations(ctx, Xd, Yd, p, steps, flush, stream):
+    """Device-resident registrations timed with CUDA events (L2 flushed before each)."""
+    import torch
+    step_ms, estep_ms, got = [], [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        got = ctx.register(Xd, Yd, p)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        estep_ms.append(ctx.last_timing()["ms_estep"])
+    return got, statistics.mean(step_ms), statistics.mean(estep_ms) / got["iters"]
 
 
 def run_ours(args):
@@ -363,13 +398,17 @@ def run_ours(args):
     t_launch = statistics.mean(estep_ms) / iters_run / 1e3
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32-pipe Top/s
-    achieved = FLOPS_PER_PAIR * N * M / t_launch / 1e12
+    # the tensor-core variant is measured against the FP32-pipe work it keeps (the moment sums
+    # run on tcgen05 at ~11 % of the tensor pipe)
+    ops = TC_FP32_OPS_PER_PAIR if args.precision == 2 else FLOPS_PER_PAIR
+    achieved = ops * N * M / t_launch / 1e12
     ex2_rate = EX2_PER_PAIR * N * M / t_launch
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": profile_traffic(),
-            "kernel": "estep_kernel", "ms_per_launch": round(t_launch * 1e3, 5),
+            "frac": round(achieved / peak, 4), "traffic": profile_traffic(args.precision, args.workload),
+            "kernel": "estep_tc_kernel" if args.precision == 2 else "estep_kernel",
+            "ms_per_launch": round(t_launch * 1e3, 5),
             "pairs_per_s_per_launch": N * M / t_launch,
-            "counted": f"{FLOPS_PER_PAIR} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, N*M pairs per launch",
+            "counted": f"{ops} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, N*M pairs per launch",
             "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)",
             "ex2_per_s": ex2_rate}
     if clk.get("sm_mhz"):
@@ -385,11 +424,37 @@ def run_ours(args):
                    "clock": "host wall"},
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
            "mode": got["mode"], "iters_run": iters_run, "e_step_plan": plan_obj(ctx), "device_ms": breakdown}
+    # the same workload with the moment sums on the tensor cores (precision 2), same protocol
+    mixed = None
+    if args.precision == 0 and not args.no_variants:
+        p2 = binding.default_params(max_iters=iters, precision=2)
+        for _ in range(max(args.warmup, 1)):
+            ctx.register(Xd, Yd, p2)
+        barrier()
+        got2, ms2, est2 = time_registrations(ctx, Xd, Yd, p2, args.steps, flush, stream)
+        barrier()
+        diag = float(np.linalg.norm(c["Y"].max(0).astype(np.float64) - c["Y"].min(0).astype(np.float64)))
+        mixed = {"precision": 2, "e_step": E_STEP_DESC[2], "dtype": DTYPE[2],
+                 "value": job_throughput(got2["iters"] * N * M, ws, ms2), "unit": UNIT, "ms_per_step": round(ms2, 4),
+                 "estep_ms_per_launch": round(est2, 5), "speedup_vs_fp32_step": round(ms / ms2, 4),
+                 "speedup_vs_fp32_estep": round(t_launch * 1e3 / est2, 4),
+                 "roofline": {"bound": "alu", "kernel": "estep_tc_kernel",
+                              "achieved": round(TC_FP32_OPS_PER_PAIR * N * M / (est2 / 1e3) / 1e12, 3),
+                              "peak": round(peak, 3), "unit": "TFLOP/s",
+                              "frac": round(TC_FP32_OPS_PER_PAIR * N * M / (est2 / 1e3) / 1e12 / peak, 4),
+                              "traffic": profile_traffic(2, args.workload),
+                              "counted": f"{TC_FP32_OPS_PER_PAIR} FP32-pipe ops + 1 EX2 per pair (the moment "
+                                         "sums run on tcgen05)"},
+                 "iters_run": got2["iters"],
+                 "vs_fp32_result": errors_vs(got2, got, diag)}
+        out["mixed_precision"] = mixed
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb, err = cpu_baseline(c, got, iters_run)
+        cb, ref = cpu_baseline(c, got, iters_run)
         out["cpu_baseline"] = cb
-        if err:
-            out["vs_fp64_oracle"] = err
+        if ref:
+            out["vs_fp64_oracle"] = errors_vs(got, ref, ref["diag"])
+            if mixed:
+                mixed["vs_fp64_oracle"] = errors_vs(got2, ref, ref["diag"])
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -512,17 +577,43 @@ def run_batch(args):
            "e_step_plan": plan,
            "per_pair_form": {"value": pp_pairs / (pp_ms / 1e3), "unit": UNIT, "ms_per_step": round(pp_ms, 3),
                              "calls": P, "batched_speedup": round((pp_ms / pp_pairs) / (ms / pairs_per_step), 3)}}
+    # the same batch with the moment sums on the tensor cores (precision 2), same protocol
+    if args.precision == 0 and not args.no_variants:
+        p2 = binding.default_params(max_iters=iters, precision=2)
+        for _ in range(max(args.warmup, 1)):
+            ctx.register_batch(Xd, n_off, Yd, m_off, p2)
+        barrier()
+        t2, est2 = [], []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            got2 = ctx.register_batch(Xd, n_off, Yd, m_off, p2)
+            e1.record(stream)
+            e1.synchronize()
+            t2.append(e0.elapsed_time(e1))
+            est2.append(ctx.last_timing()["ms_estep"])
+        barrier()
+        ms2 = statistics.mean(t2)
+        it2 = int(got2["iters"].max())
+        rot = [oracle_rot(got2["R"][i], got["R"][i]) for i in range(P)]
+        out["mixed_precision"] = {
+            "precision": 2, "e_step": E_STEP_DESC[2], "dtype": DTYPE[2],
+            "value": job_throughput(float((got2["iters"].astype(np.float64) * nm).sum()), ws, ms2), "unit": UNIT,
+            "ms_per_step": round(ms2, 4), "estep_ms_per_launch": round(statistics.mean(est2) / it2, 5),
+            "speedup_vs_fp32_step": round(ms / ms2, 4), "max_rot_err_vs_fp32_rad": float(max(rot))}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         # the oracle on one pair of the batch (the largest one whose full registration fits the budget)
         order = np.argsort(-nm)
         i = int(order[min(len(order) - 1, 8)])
         q = pairs[i]
         gi = {"R": got["R"][i], "t": got["t"][i], "sigma2": float(got["sigma2"][i])}
-        cb, err = cpu_baseline(q, gi, int(got["iters"][i]), budget_s=30.0)
+        cb, ref = cpu_baseline(q, gi, int(got["iters"][i]), budget_s=30.0)
         cb["sample"] = f"pair {i} of the batch (N={len(q['X'])}, M={len(q['Y'])}): " + cb["sample"]
         out["cpu_baseline"] = cb
-        if err:
-            out["vs_fp64_oracle"] = dict(err, pair=i)
+        if ref:
+            out["vs_fp64_oracle"] = dict(errors_vs(gi, ref, ref["diag"]), pair=i)
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -45,10 +45,11 @@
 namespace lsg {
 namespace {
 
-constexpr int kTcWarps = 8;   // compute warps
-constexpr int kTcS = 4;       // sources per compute thread
-constexpr int kTcSB = kTcWarps * 32 * kTcS;
-constexpr int kTcThreads = (kTcWarps + 2) * 32;
+constexpr int kTcSB = 1024;   // sources per block (the plan with 4 sources per thread)
+#ifndef LSG_TC_CW
+#define LSG_TC_CW 16
+#endif
+constexpr int kTcCW = LSG_TC_CW;  // compute warps (8 or 16)
 constexpr int kTcStages = 6;  // 6 x 19.5 KB: also keeps the CTA alone on its SM
 constexpr int kFeatRows = 32;
 constexpr int kFeatFloats = kFeatRows * kTile;  // per tile
@@ -62,7 +63,6 @@ constexpr uint32_t kACol = 256;
 constexpr size_t kTcSmem = static_cast<size_t>(kTcStages) * kStageBytes + (2 * kTcStages + 7) * 8 + 16;
 
 static_assert(kStageBytes % 128 == 0, "stages stay 128-byte aligned");
-static_assert(kTcSB == 1024, "the source block of the plan with 4 sources per thread");
 
 // Feature rows (B operand, one row per feature, K = target):
 //   0 one | 1-3 b hi | 4-9 a a^T hi | 10-12 b lo | 13-18 a a^T lo | 19 lambda hi | 20 lambda lo | 21-31 zero
@@ -107,16 +107,21 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
-// Bounded wait that also gives up once another role of the CTA has aborted.
+// Bounded wait that also gives up once another role of the CTA has aborted.  Each
+// try_wait may suspend the thread for up to kSuspendNs (it resumes as soon as the
+// phase completes), so a waiting thread does not take issue slots from the
+// compute warps of its scheduler.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
   const uint32_t a = smem_addr(bar);
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (ok) return true;
     if (*abort_flag) return false;
@@ -174,13 +179,17 @@ struct Cursor {  // source block of a unit; units advance monotonically
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // MODE: 0 uniform shift, 1 per-source shift L_n (El accumulated through the lambda feature).
-template <int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
+// CW compute warps with S = 1024 / (32 CW) sources per thread: (8, 4) or (16, 2); either way
+// the sources of a block form 8 matrices of 128 rows.
+template <int MODE, int CW>
+__global__ void __launch_bounds__((CW + 2) * 32, 1)
     estep_tc_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const float* __restrict__ feat,
                     const EmState* __restrict__ st, const float* __restrict__ ls_n, float* __restrict__ part,
                     const int* __restrict__ tab, const int* __restrict__ done_count, int* __restrict__ status,
                     Geo g) {
   constexpr int SB = kTcSB;
+  constexpr int S = SB / (32 * CW);
+  static_assert(S * 32 * CW == SB && CW % 4 == 0 && (CW / 4) * S == 8, "8 matrices of 128 sources");
   constexpr int H = kTile / 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kTcStages * kStageBytes);
@@ -211,19 +220,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int i = 0; i < kTcStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kTcWarps + 1);
+      mbar_init(&empty[i], CW + 1);
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&a_full[i], kTcWarps);
+      mbar_init(&a_full[i], CW);
       mbar_init(&a_empty[i], 1);
     }
     mbar_init(d_full, 1);
-    mbar_init(d_empty, kTcWarps);
+    mbar_init(d_empty, CW);
     mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == kTcWarps + 1) {
+  if (warp == CW + 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -233,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == kTcWarps) {
+  if (warp == CW) {
     // ---------------- producer ----------------
     if (lane == 0) {
       Cursor cur{first_block};
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         mbar_wait(&full[j % kTcStages], static_cast<uint32_t>(j / kTcStages) & 1u);
     }
     __syncwarp();
-  } else if (warp == kTcWarps + 1) {
+  } else if (warp == CW + 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       Cursor cur{first_block};
@@ -325,12 +334,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncwarp();
   } else {
     // ---------------- compute warps ----------------
+    // The exponentials of chunk c go to TMEM right after they are computed; the
+    // wait for that store and the hand-over to the MMA thread (a_full) come after
+    // chunk c + 1 is computed, so the store overlaps the arithmetic.
     const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const uint32_t mi0 = 4u * static_cast<uint32_t>(warp >> 2);
+    const uint32_t mi0 = static_cast<uint32_t>(S * (warp >> 2));
     Cursor cur{first_block};
     long long u = u0;
     int i = 0, cc = 0, seg = 0;
+    int pending = -1;  // buffer whose store is not yet handed over
     bool ok = true;
+    auto hand_over = [&]() {
+      if (pending >= 0) {
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[pending]);
+        pending = -1;
+      }
+    };
     while (ok && u < u1) {
       const int b = cur.advance(unit_off, u);
       const EmState* sp = st + block_pair[b];
@@ -344,10 +366,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int q = 0; q < 9; ++q) Rm[q] = sp->Rf[q];
 #pragma unroll
       for (int q = 0; q < 3; ++q) tv[q] = sp->tf[q];
-      float2 z0[kTcS], z1[kTcS], z2[kTcS], ls[kTcS], dq[kTcS];
+      float2 z0[S], z1[S], z2[S], ls[S], dq[S];
 #pragma unroll
-      for (int s = 0; s < kTcS; ++s) {
-        const long long n = static_cast<long long>(b) * SB + warp * 32 * kTcS + s * 32 + lane;
+      for (int s = 0; s < S; ++s) {
+        const long long n = static_cast<long long>(b) * SB + warp * 32 * S + s * 32 + lane;
         const float4 x = xs[n];
         // z = R x + t in FP32 (centred frame of the pair), scaled by sqrt(c)
         const float a0 = fmaf(Rm[0], x.x, fmaf(Rm[1], x.y, fmaf(Rm[2], x.z, tv[0])));
@@ -368,55 +390,62 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float2* T2 = reinterpret_cast<const float2*>(smem_raw + stage * kStageBytes + kFeatFloats * 4);
         for (int c = 0; c < kChunks; ++c, ++cc) {
           const int buf = cc & 1;
+          float ev[S][kChunk];
+          if (live) {  // a finished pair keeps the hand-shakes only
+#pragma unroll
+          for (int p = 0; p < kChunk / 2; ++p) {
+            const int q = c * (kChunk / 2) + p;
+            const float2 ny0 = T2[0 * H + q], ny1 = T2[1 * H + q], ny2 = T2[2 * H + q];
+            const float2 lam = T2[3 * H + q];
+            const float2 ta0 = T2[4 * H + q], ta1 = T2[5 * H + q], ta2 = T2[6 * H + q];
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              const float2 r0 = __fadd2_rn(z0[s], ny0);
+              const float2 r1 = __fadd2_rn(z1[s], ny1);
+              const float2 r2 = __fadd2_rn(z2[s], ny2);
+              float2 v = __fmul2_rn(ta0, r0);  // v = a . r^
+              v = __ffma2_rn(ta1, r1, v);
+              v = __ffma2_rn(ta2, r2, v);
+              float2 qq = MODE ? __fadd2_rn(lam, ls[s]) : lam;  // q = c d + lambda_m (+ L_n)
+              qq = __ffma2_rn(r0, r0, qq);
+              qq = __ffma2_rn(r1, r1, qq);
+              qq = __ffma2_rn(r2, r2, qq);
+              qq = __ffma2_rn(v, v, qq);
+              float2 e;
+              e.x = tf32_trunc(ex2_neg(qq.x));
+              e.y = tf32_trunc(ex2_neg(qq.y));
+              dq[s] = __ffma2_rn(e, qq, dq[s]);
+              ev[s][2 * p] = e.x;
+              ev[s][2 * p + 1] = e.y;
+            }
+          }
+          }
+          hand_over();  // the previous chunk
+          // this chunk's buffer is free once the MMAs of chunk cc - 2 have completed (also waited
+          // for when nothing is stored: the arrivals on a_full must not run ahead of the MMA thread
+          // by more than one phase)
           if (cc >= 2 && !__all_sync(0xffffffffu, tc_wait(&a_empty[buf], static_cast<uint32_t>((cc >> 1) - 1) & 1u,
                                                           abort_flag))) {
             ok = false;
             break;
           }
           if (live) {
-            tc_fence_after();  // the MMAs that read this buffer have completed
-            float ev[kTcS][kChunk];
+            tc_fence_after();
 #pragma unroll
-            for (int p = 0; p < kChunk / 2; ++p) {
-              const int q = c * (kChunk / 2) + p;
-              const float2 ny0 = T2[0 * H + q], ny1 = T2[1 * H + q], ny2 = T2[2 * H + q];
-              const float2 lam = T2[3 * H + q];
-              const float2 ta0 = T2[4 * H + q], ta1 = T2[5 * H + q], ta2 = T2[6 * H + q];
-#pragma unroll
-              for (int s = 0; s < kTcS; ++s) {
-                const float2 r0 = __fadd2_rn(z0[s], ny0);
-                const float2 r1 = __fadd2_rn(z1[s], ny1);
-                const float2 r2 = __fadd2_rn(z2[s], ny2);
-                float2 v = __fmul2_rn(ta0, r0);  // v = a . r^
-                v = __ffma2_rn(ta1, r1, v);
-                v = __ffma2_rn(ta2, r2, v);
-                float2 qq = MODE ? __fadd2_rn(lam, ls[s]) : lam;  // q = c d + lambda_m (+ L_n)
-                qq = __ffma2_rn(r0, r0, qq);
-                qq = __ffma2_rn(r1, r1, qq);
-                qq = __ffma2_rn(r2, r2, qq);
-                qq = __ffma2_rn(v, v, qq);
-                float2 e;
-                e.x = tf32_trunc(ex2_neg(qq.x));
-                e.y = tf32_trunc(ex2_neg(qq.y));
-                dq[s] = __ffma2_rn(e, qq, dq[s]);
-                ev[s][2 * p] = e.x;
-                ev[s][2 * p + 1] = e.y;
-              }
-            }
-#pragma unroll
-            for (int s = 0; s < kTcS; ++s)
-              tc_st16(tmem + lane_base + kACol + 128u * buf + 16u * (mi0 + s), ev[s]);
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            for (int s = 0; s < S; ++s) tc_st16(tmem + lane_base + kACol + 128u * buf + 16u * (mi0 + s), ev[s]);
+            pending = buf;
+          } else {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[buf]);
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&a_full[buf]);
         }
         if (!ok) break;
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[stage]);
+        if (lane == 0) mbar_arrive(&empty[stage]);  // the record planes of this tile are no longer read
       }
       if (!ok) break;
+      hand_over();
       // segment end: the accumulators of this thread's sources
       if (!__all_sync(0xffffffffu, tc_wait(d_full, static_cast<uint32_t>(seg) & 1u, abort_flag))) {
         ok = false;
@@ -426,10 +455,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (live) {
         float* dst = part + static_cast<size_t>(first_slot + seg) * kMom * SB;
 #pragma unroll
-        for (int s = 0; s < kTcS; ++s) {
+        for (int s = 0; s < S; ++s) {
           float d[32];
           tc_ld32(tmem + lane_base + kDCol + 32u * (mi0 + s), d);
-          const int nl = warp * 32 * kTcS + s * 32 + lane;
+          const int nl = warp * 32 * S + s * 32 + lane;
           dst[0 * SB + nl] = d[0];
 #pragma unroll
           for (int k = 0; k < 3; ++k) dst[(1 + k) * SB + nl] = d[1 + k] + d[10 + k];
@@ -444,14 +473,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) mbar_arrive(d_empty);
       ++seg;
     }
-    if (!ok && lane == 0) {
-      atomicOr(status, kStatusTimeout);
-      *abort_flag = 1;
+    if (!ok) {
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");  // no store of this thread in flight
+      if (lane == 0) {
+        atomicOr(status, kStatusTimeout);
+        *abort_flag = 1;
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == kTcWarps + 1) {
+  if (warp == CW + 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
@@ -505,24 +537,24 @@ cudaError_t launch_features(const BatchPlan& p, const float* rec, const float4* 
   return cudaGetLastError();
 }
 
+namespace {
+template <int MODE, int CW>
+cudaError_t launch_tc_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, const float* feat,
+                        const float* ls_n, float* part, int* status, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(estep_tc_kernel<MODE, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kTcSmem));
+  if (e != cudaSuccess) return e;
+  estep_tc_kernel<MODE, CW><<<p.g.grid, (CW + 2) * 32, kTcSmem, s>>>(xs, rec, feat, d.st, ls_n, part, d.tab,
+                                                                       d.done_count, status, p.g);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_estep_tc(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, const float* feat,
                             int mode, const float* ls_n, float* part, int* status, cudaStream_t s) {
   if (p.g.SB != kTcSB) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (mode) {
-    e = cudaFuncSetAttribute(estep_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kTcSmem));
-    if (e != cudaSuccess) return e;
-    estep_tc_kernel<1><<<p.g.grid, kTcThreads, kTcSmem, s>>>(xs, rec, feat, d.st, ls_n, part, d.tab, d.done_count,
-                                                             status, p.g);
-  } else {
-    e = cudaFuncSetAttribute(estep_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kTcSmem));
-    if (e != cudaSuccess) return e;
-    estep_tc_kernel<0><<<p.g.grid, kTcThreads, kTcSmem, s>>>(xs, rec, feat, d.st, nullptr, part, d.tab,
-                                                             d.done_count, status, p.g);
-  }
-  return cudaGetLastError();
+  if (mode) return launch_tc_t<1, kTcCW>(p, d, xs, rec, feat, ls_n, part, status, s);
+  return launch_tc_t<0, kTcCW>(p, d, xs, rec, feat, nullptr, part, status, s);
 }
 
 }  // namespace lsg
