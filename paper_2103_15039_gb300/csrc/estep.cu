@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(kShiftThreads)
 // cross-row reduction.
 // ---------------------------------------------------------------------------
 constexpr int kCombineThreads = kCombineSources;
+constexpr int kCombineUnroll = 4;
 constexpr int kCombineWarps = kCombineThreads / 32;
 constexpr int kCPad = kGlob + 1;  // odd row pitch: conflict-free transposition
 
@@ -404,15 +405,27 @@ __global__ void __launch_bounds__(kCombineThreads)
   if (valid) {
     const int first = tab[g.o_block_slot + 2 * b];
     const int count = tab[g.o_block_slot + 2 * b + 1];
-    for (int j = first; j < first + count; ++j) {
-      const float* src = part + static_cast<size_t>(j) * kMom * g.SB + nl;
+    // Kahan summation of the pieces, in slot order; the loads of up to kCombineUnroll slots
+    // are issued before they are summed (the sums are latency-bound on L2 otherwise)
+    for (int j0 = first; j0 < first + count; j0 += kCombineUnroll) {
+      float v[kCombineUnroll][kMom];
 #pragma unroll
-      for (int k = 0; k < kMom; ++k) {  // Kahan summation of the pieces
-        if (k < nmom) {
-          const float y = src[static_cast<size_t>(k) * g.SB] - cmp[k];
-          const float t = m[k] + y;
-          cmp[k] = (t - m[k]) - y;
-          m[k] = t;
+      for (int jj = 0; jj < kCombineUnroll; ++jj) {
+        const bool in = j0 + jj < first + count;
+        const float* src = part + static_cast<size_t>(in ? j0 + jj : first) * kMom * g.SB + nl;
+#pragma unroll
+        for (int k = 0; k < kMom; ++k) v[jj][k] = (in && k < nmom) ? __ldg(src + static_cast<size_t>(k) * g.SB) : 0.f;
+      }
+#pragma unroll
+      for (int jj = 0; jj < kCombineUnroll; ++jj) {
+        if (j0 + jj < first + count) {
+#pragma unroll
+          for (int k = 0; k < kMom; ++k) {
+            const float y = v[jj][k] - cmp[k];
+            const float t = m[k] + y;
+            cmp[k] = (t - m[k]) - y;
+            m[k] = t;
+          }
         }
       }
     }

@@ -52,17 +52,17 @@ __device__ const double c_exp_series[3][9] = {
 // Built at compile time from the closed forms in the file comment.
 struct HessTab {
   int ic[27][4];
-  double cc[27][4];
+  float cc[27][4];
   int in[27][3];
-  double cn[27][3];
+  float cn[27][3];
 };
 
 __host__ __device__ constexpr int pair_q_c(int k, int l) {
   return k > l ? pair_q_c(l, k) : (k == 0 ? l : (k == 1 ? 3 + l : (k == 2 ? 5 + l : 9)));
 }
 __host__ __device__ constexpr int cflat(int k, int l, int i, int j) { return pair_q_c(k, l) * 9 + 3 * i + j; }
-__host__ __device__ constexpr double eps_c(int a, int b, int c) {
-  return (a == b || b == c || a == c) ? 0.0 : (((b - a + 3) % 3 == 1) ? 1.0 : -1.0);
+__host__ __device__ constexpr float eps_c(int a, int b, int c) {
+  return (a == b || b == c || a == c) ? 0.f : (((b - a + 3) % 3 == 1) ? 1.f : -1.f);
 }
 
 __host__ __device__ constexpr HessTab make_hess_tab() {
@@ -70,22 +70,22 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
   for (int e = 0; e < 27; ++e)
     for (int t = 0; t < 4; ++t) {
       h.ic[e][t] = 0;
-      h.cc[e][t] = 0.0;
+      h.cc[e][t] = 0.f;
       if (t < 3) {
         h.in[e][t] = 0;
-        h.cn[e][t] = 0.0;
+        h.cn[e][t] = 0.f;
       }
     }
   for (int a = 0; a < 6; ++a) {  // gradient
     if (a < 3) {
       const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
       h.in[a][0] = 4 * a2 + a1;
-      h.cn[a][0] = 2.0;
+      h.cn[a][0] = 2.f;
       h.in[a][1] = 4 * a1 + a2;
-      h.cn[a][1] = -2.0;
+      h.cn[a][1] = -2.f;
     } else {
       h.in[a][0] = 4 * (a - 3) + 3;
-      h.cn[a][0] = 2.0;
+      h.cn[a][0] = 2.f;
     }
   }
   int e = 6;
@@ -95,30 +95,30 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
       if (b < 3) {
         const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
         h.ic[e][0] = cflat(a2, b2, a1, b1);
-        h.cc[e][0] = 2.0;
+        h.cc[e][0] = 2.f;
         h.ic[e][1] = cflat(a2, b1, a1, b2);
-        h.cc[e][1] = -2.0;
+        h.cc[e][1] = -2.f;
         h.ic[e][2] = cflat(a1, b2, a2, b1);
-        h.cc[e][2] = -2.0;
+        h.cc[e][2] = -2.f;
         h.ic[e][3] = cflat(a1, b1, a2, b2);
-        h.cc[e][3] = 2.0;
+        h.cc[e][3] = 2.f;
         if (a != b) {  // N_ab + N_ba
           h.in[e][0] = 4 * a + b;
-          h.cn[e][0] = 1.0;
+          h.cn[e][0] = 1.f;
           h.in[e][1] = 4 * b + a;
-          h.cn[e][1] = 1.0;
+          h.cn[e][1] = 1.f;
         } else {  // 2 N_aa - 2 tr N
           for (int i = 0; i < 3; ++i) {
             h.in[e][i] = 5 * i;
-            h.cn[e][i] = (i == a) ? 0.0 : -2.0;
+            h.cn[e][i] = (i == a) ? 0.f : -2.f;
           }
         }
       } else if (a < 3) {
         const int c = b - 3;
         h.ic[e][0] = cflat(a1, 3, a2, c);
-        h.cc[e][0] = 2.0;
+        h.cc[e][0] = 2.f;
         h.ic[e][1] = cflat(a2, 3, a1, c);
-        h.cc[e][1] = -2.0;
+        h.cc[e][1] = -2.f;
         if (c != a) {
           const int i = 3 - a - c;
           h.in[e][0] = 4 * i + 3;
@@ -126,7 +126,7 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
         }
       } else {
         h.ic[e][0] = cflat(3, 3, a - 3, b - 3);
-        h.cc[e][0] = 2.0;
+        h.cc[e][0] = 2.f;
       }
     }
   return h;
@@ -134,30 +134,89 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
 
 __device__ const HessTab c_hess = make_hess_tab();
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the Newton loop: a value is hi + lo (|lo| at most
+// half an ulp of hi), about 48 significant bits, computed on the FP32 pipe with
+// the error-free transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the
+// FMA-based exact product.  GB300 issues FP64 instructions far more slowly than
+// FP32 ones and the loop is a chain of dependent operations, so its state, the
+// model it needs for the objective change, and every operation on them use
+// these pairs; the Hessian only steers the direction and is FP32.
+// ---------------------------------------------------------------------------
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd dd_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - static_cast<double>(h))};
+}
+__device__ __forceinline__ double dd_to(dd a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+__device__ __forceinline__ float dd_f(dd a) { return __fadd_rn(a.hi, a.lo); }
+
+__device__ __forceinline__ dd two_sum(float a, float b) {  // s + e = a + b exactly
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd two_prod(float a, float b) {  // p + e = a b exactly
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  const dd t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_mulf(dd a, float b) {  // b exact in FP32
+  dd p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+__device__ __forceinline__ dd dd_scale2(dd a, float s) { return {a.hi * s, a.lo * s}; }  // s a power of two
+__device__ __forceinline__ bool dd_le0(dd a) { return a.hi < 0.f || (a.hi == 0.f && a.lo <= 0.f); }
+
+// theta^2 = w . w for a rotation part given exactly in FP32
+__device__ __forceinline__ dd theta2(const float* w) {
+  return dd_add(dd_add(two_prod(w[0], w[0]), two_prod(w[1], w[1])), two_prod(w[2], w[2]));
+}
+
 struct Shared {
   double SD, NP;
   double H1[12];
-  double A[10][6];  // A^{q}, q = xt pair (00,01,02,03,11,12,13,22,23,33), entries (00,01,02,11,12,22)
-  double R[9], t[3];
-  double Ro[9], to[3];
-  double M1[12];
+  double R[9], t[3];    // the pose in FP64 (start and result of the Newton loop)
+  double Ro[9], to[3];  // the E step's pose T_o
   double Q;
-  double C[10][9];
-  double NM[12];
-  double gH[27];   // grad (6) then the upper triangle of H_s (21)
-  float gHf[27];   // the same in FP32 for the direction solve
-  float xf[6];     // Newton direction (FP32)
-  double xi[6];
-  double coef[3];  // exp coefficients
-  double wv[6];    // scaled step
-  double E[9], Vv[3];
-  double Tc[12], dl[12], Gd[12];
-  double dQ;
+  float gHf[27];  // gradient (6) then the upper triangle of H_s (21), FP32 for the direction solve
+  float xf[6];    // Newton direction (FP32)
+  float wv[6];    // step * xi (exact in FP32)
+  float Af[10][6];  // model in FP32 for the Hessian: A^{q}, q = xt pair (00,01,02,03,11,12,13,22,23,33),
+                    // entries (00,01,02,11,12,22)
+  float Cf[10][9];  // C^{kl} = R^T A^{kl} R (FP32, Hessian only)
+  float NMf[12];
   int iters, damped, halvings;
   int go;          // loop control
   int accepted;
   HessTab hess;    // per-lane divergent lookups: shared, not constant, memory
-  double series[3][9];
+  // double-float state of the loop (hi, lo pairs)
+  dd Ad[10][6];  // the model for G D
+  dd Rd[9], td[3], M1d[12], NMd[12], Qd, dQd;
+  dd coefd[3], Ed[9], Vvd[3], Tcd[12], dld[12], Gdd[12], dqv[12];
+  dd seriesd[3][9];
 };
 
 // position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
@@ -194,8 +253,13 @@ __device__ void load_model(Shared& s, const double* mom) {
     const int* src = reinterpret_cast<const int*>(&c_hess);
     int* dst = reinterpret_cast<int*>(&s.hess);
     // global (not constant) memory: every lane reads a different word, so the loads coalesce
-    for (int i = tid; i < static_cast<int>(sizeof(HessTab) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(src + i);
-    if (tid < 27) s.series[tid / 9][tid % 9] = __ldg(&c_exp_series[tid / 9][tid % 9]);
+    constexpr int kWords = static_cast<int>(sizeof(HessTab) / sizeof(int));
+#pragma unroll
+    for (int r = 0; r < (kWords + kMThreads - 1) / kMThreads; ++r) {  // all loads in flight at once
+      const int i = tid + r * kMThreads;
+      if (i < kWords) dst[i] = __ldg(src + i);
+    }
+    if (tid < 27) s.seriesd[tid / 9][tid % 9] = dd_from(__ldg(&c_exp_series[tid / 9][tid % 9]));
   }
   if (tid == 0) {
     s.NP = mom[0];
@@ -204,7 +268,9 @@ __device__ void load_model(Shared& s, const double* mom) {
   if (tid < 12) s.H1[tid] = mom[2 + tid];
   if (tid < 60) {
     const int p = tid / 10, q = tid % 10;  // moments are ordered A pair major, xt pair minor
-    s.A[q][p] = mom[14 + tid];
+    const double a = mom[14 + tid];
+    s.Ad[q][p] = dd_from(a);
+    s.Af[q][p] = static_cast<float>(a);
   }
 }
 
@@ -256,6 +322,7 @@ __device__ __forceinline__ bool ldl_solve6(const float (&H)[36], const float (&b
 }
 
 // Newton loop on the model in shared memory; T starts at (s.R, s.t) == (s.Ro, s.to).
+// Ends with s.R, s.t and s.Q (FP64) set from the double-float state.
 __device__ void newton(Shared& s, int newton_max, double newton_tol) {
   const int tid = threadIdx.x;
   // lane tid < 12 owns (G D)_ik, i = tid / 4, k = tid % 4: its 12 model entries
@@ -268,50 +335,55 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) gidx[3 * l + j] = pair_q(k, l) * 6 + sym_p(i, j);
   }
-  // the model does not change during the loop: lanes < 12 keep their 12 entries in registers
-  double ga[12];
-  {
-    const double* Af = &s.A[0][0];
-#pragma unroll
-    for (int j = 0; j < 12; ++j) ga[j] = tid < 12 ? Af[gidx[j]] : 0.0;
-  }
-  if (tid < 12) s.M1[tid] = s.H1[tid];
-  if (tid == 0) {
-    s.Q = s.SD;
+  if (tid < 12) s.M1d[tid] = dd_from(s.H1[tid]);
+  if (tid < 9) {
+    s.Rd[tid] = dd_from(s.R[tid]);
+  } else if (tid < 12) {
+    s.td[tid - 9] = dd_from(s.t[tid - 9]);
+  } else if (tid == 32) {
+    s.Qd = dd_from(s.SD);
     s.iters = s.damped = s.halvings = 0;
     s.go = 1;
   }
   __syncthreads();
   for (int it = 0; it < newton_max; ++it) {
-    // --- C^{kl} = R^T A^{kl} R (60 unique entries) and N, m = R^T M1 ---
+    // --- C^{kl} = R^T A^{kl} R (FP32: Hessian only) and N, m = R^T M1 (double-float) ---
     if (tid < 60) {
       const int q = tid / 6, p = tid % 6;
       const int i = p < 3 ? 0 : (p < 5 ? 1 : 2);
       const int j = p < 3 ? p : (p < 5 ? p - 2 : 2);
-      const double* Aq = s.A[q];
+      const float* Aq = s.Af[q];
       // u = A^q R e_j, then v = (R e_i) . u
-      const double r0 = s.R[j], r1 = s.R[3 + j], r2 = s.R[6 + j];
-      const double u0 = Aq[0] * r0 + Aq[1] * r1 + Aq[2] * r2;
-      const double u1 = Aq[1] * r0 + Aq[3] * r1 + Aq[4] * r2;
-      const double u2 = Aq[2] * r0 + Aq[4] * r1 + Aq[5] * r2;
-      const double v = s.R[i] * u0 + s.R[3 + i] * u1 + s.R[6 + i] * u2;
-      s.C[q][3 * i + j] = v;
-      s.C[q][3 * j + i] = v;
+      const float r0 = s.Rd[j].hi, r1 = s.Rd[3 + j].hi, r2 = s.Rd[6 + j].hi;
+      const float u0 = fmaf(Aq[0], r0, fmaf(Aq[1], r1, Aq[2] * r2));
+      const float u1 = fmaf(Aq[1], r0, fmaf(Aq[3], r1, Aq[4] * r2));
+      const float u2 = fmaf(Aq[2], r0, fmaf(Aq[4], r1, Aq[5] * r2));
+      const float v = fmaf(s.Rd[i].hi, u0, fmaf(s.Rd[3 + i].hi, u1, s.Rd[6 + i].hi * u2));
+      s.Cf[q][3 * i + j] = v;
+      s.Cf[q][3 * j + i] = v;
     } else if (tid >= 64 && tid < 76) {
       const int e = tid - 64, i = e / 4, k = e % 4;
-      s.NM[e] = s.R[i] * s.M1[k] + s.R[3 + i] * s.M1[4 + k] + s.R[6 + i] * s.M1[8 + k];
+      dd v = dd_mul(s.Rd[i], s.M1d[k]);
+      v = dd_fma(s.Rd[3 + i], s.M1d[4 + k], v);
+      v = dd_fma(s.Rd[6 + i], s.M1d[8 + k], v);
+      s.NMd[e] = v;
+      s.NMf[e] = dd_f(v);
     }
     __syncthreads();
-    // --- gradient (6) and the upper triangle of H_s (21): branch-free table form ---
-    if (tid < 27) {
-      const double* Cf = &s.C[0][0];
-      double v = 0.0;
+    // --- gradient (6, double-float, rounded for the FP32 solve) and the upper triangle of
+    // H_s (21, FP32): branch-free table form ---
+    if (tid < 6) {
+      dd v{0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < 4; ++t) v = fma(s.hess.cc[tid][t], Cf[s.hess.ic[tid][t]], v);
+      for (int t = 0; t < 3; ++t) v = dd_add(v, dd_scale2(s.NMd[s.hess.in[tid][t]], s.hess.cn[tid][t]));
+      s.gHf[tid] = dd_f(v);
+    } else if (tid < 27) {
+      float v = 0.f;
 #pragma unroll
-      for (int t = 0; t < 3; ++t) v = fma(s.hess.cn[tid][t], s.NM[s.hess.in[tid][t]], v);
-      s.gH[tid] = v;
-      s.gHf[tid] = static_cast<float>(v);
+      for (int t = 0; t < 4; ++t) v = fmaf(s.hess.cc[tid][t], (&s.Cf[0][0])[s.hess.ic[tid][t]], v);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) v = fmaf(s.hess.cn[tid][t], s.NMf[s.hess.in[tid][t]], v);
+      s.gHf[tid] = v;
     }
     __syncthreads();
     // --- Newton direction (FP32 LDL^T, damped if not positive definite) ---
@@ -357,95 +429,107 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     }
     __syncthreads();
     if (!s.go) break;
-    // --- backtracking on the exact FP64 change of Q_d ---
-    double step = 1.0;
-    for (int bt = 0; bt <= 10; ++bt, step *= 0.5) {
-      if (tid < 6) s.wv[tid] = step * static_cast<double>(s.xf[tid]);
+    // --- backtracking on the exact change of Q_d (double-float) ---
+    float step = 1.f;  // a power of two: step * xi is exact in FP32
+    for (int bt = 0; bt <= 10; ++bt, step *= 0.5f) {
+      if (tid < 6) s.wv[tid] = step * s.xf[tid];
       __syncthreads();
       if (tid < 3) {
         // exp coefficients A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3 as
-        // power series in th^2 (Horner, converged to FP64 for th <= 0.5), else from sincos
-        const double* w = s.wv;
-        const double x = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        double cf;
-        if (x <= 0.25) {
-          const double* c = s.series[tid];
-          double r = c[8];
-#pragma unroll
-          for (int k = 7; k >= 0; --k) r = fma(r, x, c[k]);
+        // power series in th^2 (Horner, with as many terms as th^2 needs for 2^-48), else from sincos
+        const dd x = theta2(s.wv);
+        dd cf;
+        if (x.hi <= 0.25f) {
+          const dd* c = s.seriesd[tid];
+          const int top = x.hi < 1e-6f ? 3 : (x.hi < 1e-3f ? 5 : 8);
+          dd r = c[top];
+          for (int k = top - 1; k >= 0; --k) r = dd_fma(r, x, c[k]);
           cf = r;
         } else {
-          const double th = sqrt(x);
+          const double xd = dd_to(x);
+          const double th = sqrt(xd);
           double sh, ch;
           sincos(0.5 * th, &sh, &ch);
           const double sn = 2.0 * sh * ch;
-          cf = tid == 0 ? sn / th : (tid == 1 ? 2.0 * sh * sh / x : (th - sn) / (x * th));
+          cf = dd_from(tid == 0 ? sn / th : (tid == 1 ? 2.0 * sh * sh / xd : (th - sn) / (xd * th)));
         }
-        s.coef[tid] = cf;
+        s.coefd[tid] = cf;
       }
       __syncthreads();
       // E = I + A W + B W^2 and V v = v + B W v + C W^2 v with W = [w]x, W^2 = w w^T - th^2 I
       if (tid < 9) {
         const int k = tid / 3, j = tid % 3;
-        const double* w = s.wv;
-        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-        // ([w]x)_kj = -eps_kjm w_m (m = 3 - k - j; zero on the diagonal)
-        const double Wkj = (k == j) ? 0.0 : -eps3(k, j, 3 - k - j) * w[3 - k - j];
-        const double W2kj = w[k] * w[j] - (k == j ? th2 : 0.0);
-        s.E[tid] = (k == j ? 1.0 : 0.0) + s.coef[0] * Wkj + s.coef[1] * W2kj;
+        const float* w = s.wv;
+        // ([w]x)_kj = -eps_kjm w_m (m = 3 - k - j; zero on the diagonal), exact in FP32
+        const float Wkj = (k == j) ? 0.f : -static_cast<float>(eps3(k, j, 3 - k - j)) * w[3 - k - j];
+        dd W2kj = two_prod(w[k], w[j]);
+        if (k == j) W2kj = dd_sub(W2kj, theta2(w));
+        dd E = dd_add(dd_mulf(s.coefd[0], Wkj), dd_mul(s.coefd[1], W2kj));
+        if (k == j) E = dd_add(E, dd{1.f, 0.f});
+        s.Ed[tid] = E;
       } else if (tid >= 32 && tid < 35) {
         const int i = tid - 32;
-        const double* w = s.wv;
-        const double* v = s.wv + 3;
-        const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        const float* w = s.wv;
+        const float* v = s.wv + 3;
         const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
-        const double Wv = w[i1] * v[i2] - w[i2] * v[i1];  // (w x v)_i
-        const double W2v = w[i] * (w[0] * v[0] + w[1] * v[1] + w[2] * v[2]) - th2 * v[i];
-        s.Vv[i] = v[i] + s.coef[1] * Wv + s.coef[2] * W2v;
+        const dd Wv = dd_sub(two_prod(w[i1], v[i2]), two_prod(w[i2], v[i1]));  // (w x v)_i
+        const dd wdv = dd_add(dd_add(two_prod(w[0], v[0]), two_prod(w[1], v[1])), two_prod(w[2], v[2]));
+        const dd W2v = dd_sub(dd_mulf(wdv, w[i]), dd_mulf(theta2(w), v[i]));
+        s.Vvd[i] = dd_add(dd_add(dd{v[i], 0.f}, dd_mul(s.coefd[1], Wv)), dd_mul(s.coefd[2], W2v));
       }
       __syncthreads();
       if (tid < 12) {  // candidate T o exp(step xi) and the difference D = T_c - T
         const int i = tid / 4, k = tid % 4;
-        double v;
-        if (k < 3)
-          v = s.R[3 * i] * s.E[k] + s.R[3 * i + 1] * s.E[3 + k] + s.R[3 * i + 2] * s.E[6 + k];
-        else
-          v = s.R[3 * i] * s.Vv[0] + s.R[3 * i + 1] * s.Vv[1] + s.R[3 * i + 2] * s.Vv[2] + s.t[i];
-        s.Tc[tid] = v;
-        s.dl[tid] = v - (k < 3 ? s.R[3 * i + k] : s.t[i]);
+        dd v;
+        if (k < 3) {
+          v = dd_mul(s.Rd[3 * i], s.Ed[k]);
+          v = dd_fma(s.Rd[3 * i + 1], s.Ed[3 + k], v);
+          v = dd_fma(s.Rd[3 * i + 2], s.Ed[6 + k], v);
+        } else {
+          v = dd_fma(s.Rd[3 * i], s.Vvd[0], s.td[i]);
+          v = dd_fma(s.Rd[3 * i + 1], s.Vvd[1], v);
+          v = dd_fma(s.Rd[3 * i + 2], s.Vvd[2], v);
+        }
+        s.Tcd[tid] = v;
+        s.dld[tid] = dd_sub(v, k < 3 ? s.Rd[3 * i + k] : s.td[i]);
       }
       __syncthreads();
       if (tid < 32) {  // G D and dQ = 2 <M1, D> + <D, G D>
-        double dq = 0.0;
         if (tid < 12) {
-          double gl[4];
+          const dd* Af = &s.Ad[0][0];
+          dd gl[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {  // four independent chains of three
-            gl[l] = ga[3 * l] * s.dl[l];
-            gl[l] = fma(ga[3 * l + 1], s.dl[4 + l], gl[l]);
-            gl[l] = fma(ga[3 * l + 2], s.dl[8 + l], gl[l]);
+            gl[l] = dd_mul(Af[gidx[3 * l]], s.dld[l]);
+            gl[l] = dd_fma(Af[gidx[3 * l + 1]], s.dld[4 + l], gl[l]);
+            gl[l] = dd_fma(Af[gidx[3 * l + 2]], s.dld[8 + l], gl[l]);
           }
-          const double g = (gl[0] + gl[1]) + (gl[2] + gl[3]);
-          s.Gd[tid] = g;
-          dq = s.dl[tid] * (2.0 * s.M1[tid] + g);
+          const dd g = dd_add(dd_add(gl[0], gl[1]), dd_add(gl[2], gl[3]));
+          s.Gdd[tid] = g;
+          s.dqv[tid] = dd_mul(s.dld[tid], dd_add(dd_scale2(s.M1d[tid], 2.f), g));
         }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) dq += __shfl_xor_sync(0xffffffffu, dq, o);
-        if (tid == 0) s.dQ = dq;
+        // fixed-order tree over the 12 terms in shared memory (a warp-shuffle tree of the
+        // pairs measured several times slower here)
+        __syncwarp();
+        if (tid < 6) s.dqv[tid] = dd_add(s.dqv[tid], s.dqv[tid + 6]);
+        __syncwarp();
+        if (tid < 3) s.dqv[tid] = dd_add(s.dqv[tid], s.dqv[tid + 3]);
+        __syncwarp();
+        if (tid == 0) s.dQd = dd_add(dd_add(s.dqv[0], s.dqv[1]), s.dqv[2]);
       }
       __syncthreads();
-      const bool acc = s.dQ <= 0.0;
+      const bool acc = dd_le0(s.dQd);
       if (acc) {
         if (tid < 12) {
           const int i = tid / 4, k = tid % 4;
           if (k < 3)
-            s.R[3 * i + k] = s.Tc[tid];
+            s.Rd[3 * i + k] = s.Tcd[tid];
           else
-            s.t[i] = s.Tc[tid];
-          s.M1[tid] += s.Gd[tid];
+            s.td[i] = s.Tcd[tid];
+          s.M1d[tid] = dd_add(s.M1d[tid], s.Gdd[tid]);
         }
         if (tid == 0) {
-          s.Q += s.dQ;
+          s.Qd = dd_add(s.Qd, s.dQd);
           s.accepted = 1;
         }
         __syncthreads();
@@ -457,12 +541,21 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
     if (tid == 0) {
       float nx = 0.f;  // |step xi|^2 of the accepted step (FP32 suffices for the test)
 #pragma unroll
-      for (int a = 0; a < 6; ++a) nx += static_cast<float>(step) * s.xf[a] * (static_cast<float>(step) * s.xf[a]);
+      for (int a = 0; a < 6; ++a) nx += (step * s.xf[a]) * (step * s.xf[a]);
       if (!s.accepted || nx < static_cast<float>(newton_tol) * static_cast<float>(newton_tol)) s.go = 0;
     }
     __syncthreads();
     if (!s.go) break;
   }
+  // the pose and objective in FP64 for the caller
+  if (tid < 9) {
+    s.R[tid] = dd_to(s.Rd[tid]);
+  } else if (tid < 12) {
+    s.t[tid - 9] = dd_to(s.td[tid - 9]);
+  } else if (tid == 32) {
+    s.Q = dd_to(s.Qd);
+  }
+  __syncthreads();
 }
 
 // One CTA per pair: its Newton M step, sigma^2 update, trace and E-step constants.
