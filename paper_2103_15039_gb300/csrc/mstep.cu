@@ -23,11 +23,14 @@
 // newton_max steps, or when no halving lowers Q_d.
 //
 // Precision (GB300 issues one FP64 warp instruction per ~64 cycles per SM
-// sub-partition): the model, the residual M1, the objective change
-// dQ = 2 <M1, D> + <D, G D> of a trial step D and the transform are FP64 and
-// computed lane-parallel; only the 6x6 solve for the Newton direction runs in
-// FP32 (LDL^T).  An inexact direction only changes the path, not the fixed
-// point, which is set by the FP64 residual (iterative refinement).
+// sub-partition, and the loop is a chain of dependent operations): the residual
+// M1, the gradient, the objective change dQ = 2 <M1, D> + <D, G D> of a trial
+// step D, the transform and Q_d are double-float values (pairs of FP32 numbers,
+// about 48 significant bits) computed lane-parallel on the FP32 pipe; the model
+// arrives in FP64 and is converted once.  The Hessian and the 6x6 solve for the
+// Newton direction (LDL^T) are FP32: an inexact direction only changes the path,
+// not the fixed point, which is set by the double-float residual (iterative
+// refinement).
 #include <math.h>
 
 #include "internal.cuh"
