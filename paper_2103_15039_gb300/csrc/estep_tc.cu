@@ -46,21 +46,23 @@ namespace lsg {
 namespace {
 
 constexpr int kTcSB = 1024;   // sources per block (the plan with 4 sources per thread)
-#ifndef LSG_TC_CW
-#define LSG_TC_CW 16
-#endif
-constexpr int kTcCW = LSG_TC_CW;  // compute warps (8 or 16)
+constexpr int kTcS = 2;        // sources per compute thread
+constexpr int kTcCW = kTcSB / (32 * kTcS);  // 16 compute warps: two halves of 8 (4 matrices of 128 sources each)
+constexpr int kHalfWarps = kTcCW / 2;
+constexpr int kMmaWarp0 = kTcCW;            // warps 16, 17: TMEM owner / MMA issuer of half 0, MMA issuer of half 1
+constexpr int kProducerWarp = kTcCW + 2;    // warp 18: bulk copies
+constexpr int kTcThreads = (kTcCW + 3) * 32;
 constexpr int kTcStages = 6;  // 6 x 19.5 KB: also keeps the CTA alone on its SM
 constexpr int kFeatRows = 32;
 constexpr int kFeatFloats = kFeatRows * kTile;  // per tile
 constexpr int kQPlanes = 7;                     // -sqrt(c) y (3), lambda, a (3): record planes 0-6
 constexpr int kQBytes = kQPlanes * kTile * 4;
 constexpr int kStageBytes = kFeatFloats * 4 + kQBytes;
-constexpr int kChunk = 16;  // targets per A buffer
+constexpr int kChunk = 32;  // targets per A buffer (one buffer per matrix)
 constexpr int kChunks = kTile / kChunk;
 constexpr uint32_t kDCol = 0;
 constexpr uint32_t kACol = 256;
-constexpr size_t kTcSmem = static_cast<size_t>(kTcStages) * kStageBytes + (2 * kTcStages + 7) * 8 + 16;
+constexpr size_t kTcSmem = static_cast<size_t>(kTcStages) * kStageBytes + (2 * kTcStages + 10) * 8 + 16;
 
 static_assert(kStageBytes % 128 == 0, "stages stay 128-byte aligned");
 
@@ -157,7 +159,7 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, u
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tc_st16(uint32_t taddr, const float (&v)[kChunk]) {
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const float (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16};" ::"r"(taddr),
@@ -190,27 +192,24 @@ struct Cursor {  // source block of a unit; units advance monotonically
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // MODE: 0 uniform shift, 1 per-source shift L_n (El accumulated through the lambda feature).
-// CW compute warps with S = 1024 / (32 CW) sources per thread: (8, 4) or (16, 2); either way
-// the sources of a block form 8 matrices of 128 rows.
-template <int MODE, int CW>
-__global__ void __launch_bounds__((CW + 2) * 32, 1)
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
     estep_tc_kernel(const float4* __restrict__ xs, const float* __restrict__ rec, const float* __restrict__ feat,
                     const EmState* __restrict__ st, const float* __restrict__ ls_n, float* __restrict__ part,
                     const int* __restrict__ tab, const int* __restrict__ done_count, int* __restrict__ status,
                     Geo g) {
   constexpr int SB = kTcSB;
-  constexpr int S = SB / (32 * CW);
-  static_assert(S * 32 * CW == SB && CW % 4 == 0 && (CW / 4) * S == 8, "8 matrices of 128 sources");
+  constexpr int S = kTcS;
   constexpr int H = kTile / 2;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kTcStages * kStageBytes);
   uint64_t* empty = full + kTcStages;
-  uint64_t* a_full = empty + kTcStages;
-  uint64_t* a_empty = a_full + 2;
-  uint64_t* d_full = a_empty + 2;
-  uint64_t* d_empty = d_full + 1;
-  uint64_t* drain = d_empty + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* a_full = empty + kTcStages;  // [half]
+  uint64_t* a_empty = a_full + 2;        // [half]
+  uint64_t* d_full = a_empty + 2;        // [half]
+  uint64_t* d_empty = d_full + 2;        // [half]
+  uint64_t* drain = d_empty + 2;         // [half]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   if (*done_count >= g.P) return;
@@ -231,19 +230,19 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
   if (tid == 0) {
     for (int i = 0; i < kTcStages; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], CW + 1);
+      mbar_init(&empty[i], kTcCW + 2);  // every compute warp and both MMA threads release a stage
     }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&a_full[i], CW);
-      mbar_init(&a_empty[i], 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&a_full[h], kHalfWarps);
+      mbar_init(&a_empty[h], 1);
+      mbar_init(&d_full[h], 1);
+      mbar_init(&d_empty[h], kHalfWarps);
+      mbar_init(&drain[h], 1);
     }
-    mbar_init(d_full, 1);
-    mbar_init(d_empty, CW);
-    mbar_init(drain, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == CW + 1) {
+  if (warp == kMmaWarp0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -253,7 +252,7 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == CW) {
+  if (warp == kProducerWarp) {
     // ---------------- producer ----------------
     if (lane == 0) {
       Cursor cur{first_block};
@@ -280,8 +279,9 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
         mbar_wait(&full[j % kTcStages], static_cast<uint32_t>(j / kTcStages) & 1u);
     }
     __syncwarp();
-  } else if (warp == CW + 1) {
-    // ---------------- MMA issuer ----------------
+  } else if (warp >= kMmaWarp0) {
+    // ---------------- MMA issuer of one half ----------------
+    const int h = warp - kMmaWarp0;
     if (lane == 0) {
       Cursor cur{first_block};
       long long u = u0;
@@ -293,8 +293,8 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
         long long seg_end = u + g.seg_cap;
         if (seg_end > unit_off[b + 1]) seg_end = unit_off[b + 1];
         if (seg_end > u1) seg_end = u1;
-        // the compute warps have read the previous segment's accumulators
-        if (seg > 0 && !tc_wait(d_empty, static_cast<uint32_t>(seg - 1) & 1u, abort_flag, kMmaSleepNs)) {
+        // the compute warps of this half have read the previous segment's accumulators
+        if (seg > 0 && !tc_wait(&d_empty[h], static_cast<uint32_t>(seg - 1) & 1u, abort_flag, kMmaSleepNs)) {
           ok = false;
           break;
         }
@@ -308,30 +308,30 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
           }
           const uint32_t fb = smem_addr(smem_raw + stage * kStageBytes);
           for (int c = 0; c < kChunks; ++c, ++cc) {
-            const int buf = cc & 1;
-            if (!tc_wait(&a_full[buf], static_cast<uint32_t>(cc >> 1) & 1u, abort_flag, kMmaSleepNs)) {
+            if (!tc_wait(&a_full[h], static_cast<uint32_t>(cc) & 1u, abort_flag, kMmaSleepNs)) {
               ok = false;
               break;
             }
             tc_fence_after();
             if (live) {
 #pragma unroll
-              for (int j = 0; j < 2; ++j) {
-                const uint64_t bd = feat_desc(fb + static_cast<uint32_t>(4 * c + 2 * j) * 128u);
+              for (int j = 0; j < kChunk / 8; ++j) {
+                const uint64_t bd = feat_desc(fb + static_cast<uint32_t>(kChunk / 4 * c + 2 * j) * 128u);
 #pragma unroll
-                for (int mi = 0; mi < 8; ++mi)
-                  tc_mma(tmem + kDCol + 32u * mi, tmem + kACol + 128u * buf + 16u * mi + 8u * j, bd,
-                         (first && j == 0) ? 0u : 1u);
+                for (int m = 0; m < 4; ++m) {
+                  const uint32_t mi = 4u * h + m;
+                  tc_mma(tmem + kDCol + 32u * mi, tmem + kACol + 32u * mi + 8u * j, bd, (first && j == 0) ? 0u : 1u);
+                }
               }
               first = false;
             }
-            tc_commit(&a_empty[buf]);
+            tc_commit(&a_empty[h]);
           }
           if (!ok) break;
           tc_commit(&empty[stage]);
         }
         if (!ok) break;
-        tc_commit(d_full);
+        tc_commit(&d_full[h]);
         ++seg;
       }
       if (!ok) {
@@ -339,31 +339,22 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
         *abort_flag = 1;
       }
       // every MMA of this thread has completed before TMEM is released
-      tc_commit(drain);
-      mbar_wait(drain, 0);
+      tc_commit(&drain[h]);
+      mbar_wait(&drain[h], 0);
     }
     __syncwarp();
   } else {
     // ---------------- compute warps ----------------
-    // The exponentials of chunk c go to TMEM right after they are computed; the
-    // wait for that store and the hand-over to the MMA thread (a_full) come after
-    // chunk c + 1 is computed, so the store overlaps the arithmetic.
+    // Half h = warp / 8 (matrices 4h .. 4h+3).  A chunk of 32 targets is computed and
+    // stored 16 at a time (two tensor-memory stores per source); the wait for the MMAs
+    // that read the buffer before comes after the first 16 are computed.
+    const int h = warp / kHalfWarps;
     const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
     const uint32_t mi0 = static_cast<uint32_t>(S * (warp >> 2));
     Cursor cur{first_block};
     long long u = u0;
     int i = 0, cc = 0, seg = 0;
-    int pending = -1;  // buffer whose store is not yet handed over
     bool ok = true;
-    auto hand_over = [&]() {
-      if (pending >= 0) {
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&a_full[pending]);
-        pending = -1;
-      }
-    };
     while (ok && u < u1) {
       const int b = cur.advance(unit_off, u);
       const EmState* sp = st + block_pair[b];
@@ -400,65 +391,68 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
         }
         const float2* T2 = reinterpret_cast<const float2*>(smem_raw + stage * kStageBytes + kFeatFloats * 4);
         for (int c = 0; c < kChunks; ++c, ++cc) {
-          const int buf = cc & 1;
-          float ev[S][kChunk];
-          if (live) {  // a finished pair keeps the hand-shakes only
 #pragma unroll
-          for (int p = 0; p < kChunk / 2; ++p) {
-            const int q = c * (kChunk / 2) + p;
-            const float2 ny0 = T2[0 * H + q], ny1 = T2[1 * H + q], ny2 = T2[2 * H + q];
-            const float2 lam = T2[3 * H + q];
-            const float2 ta0 = T2[4 * H + q], ta1 = T2[5 * H + q], ta2 = T2[6 * H + q];
+          for (int half = 0; half < 2; ++half) {
+            float ev[S][16];
+            if (live) {
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
-              const float2 r0 = __fadd2_rn(z0[s], ny0);
-              const float2 r1 = __fadd2_rn(z1[s], ny1);
-              const float2 r2 = __fadd2_rn(z2[s], ny2);
-              float2 v = __fmul2_rn(ta0, r0);  // v = a . r^
-              v = __ffma2_rn(ta1, r1, v);
-              v = __ffma2_rn(ta2, r2, v);
-              float2 qq = MODE ? __fadd2_rn(lam, ls[s]) : lam;  // q = c d + lambda_m (+ L_n)
-              qq = __ffma2_rn(r0, r0, qq);
-              qq = __ffma2_rn(r1, r1, qq);
-              qq = __ffma2_rn(r2, r2, qq);
-              qq = __ffma2_rn(v, v, qq);
-              float2 e;
-              e.x = tf32_trunc(ex2_neg(qq.x));
-              e.y = tf32_trunc(ex2_neg(qq.y));
-              dq[s] = __ffma2_rn(e, qq, dq[s]);
-              ev[s][2 * p] = e.x;
-              ev[s][2 * p + 1] = e.y;
+              for (int p = 0; p < 8; ++p) {
+                const int q = c * (kChunk / 2) + half * 8 + p;
+                const float2 ny0 = T2[0 * H + q], ny1 = T2[1 * H + q], ny2 = T2[2 * H + q];
+                const float2 lam = T2[3 * H + q];
+                const float2 ta0 = T2[4 * H + q], ta1 = T2[5 * H + q], ta2 = T2[6 * H + q];
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                  const float2 r0 = __fadd2_rn(z0[s], ny0);
+                  const float2 r1 = __fadd2_rn(z1[s], ny1);
+                  const float2 r2 = __fadd2_rn(z2[s], ny2);
+                  float2 v = __fmul2_rn(ta0, r0);  // v = a . r^
+                  v = __ffma2_rn(ta1, r1, v);
+                  v = __ffma2_rn(ta2, r2, v);
+                  float2 qq = MODE ? __fadd2_rn(lam, ls[s]) : lam;  // q = c d + lambda_m (+ L_n)
+                  qq = __ffma2_rn(r0, r0, qq);
+                  qq = __ffma2_rn(r1, r1, qq);
+                  qq = __ffma2_rn(r2, r2, qq);
+                  qq = __ffma2_rn(v, v, qq);
+                  float2 e;
+                  e.x = tf32_trunc(ex2_neg(qq.x));
+                  e.y = tf32_trunc(ex2_neg(qq.y));
+                  dq[s] = __ffma2_rn(e, qq, dq[s]);
+                  ev[s][2 * p] = e.x;
+                  ev[s][2 * p + 1] = e.y;
+                }
+              }
+            }
+            if (half == 0 && cc > 0) {
+              // the buffer is free once the MMAs of the previous chunk have completed (also
+              // waited for when nothing is stored, so that the arrivals on a_full stay one
+              // phase ahead of the MMA thread at most)
+              if (!__all_sync(0xffffffffu,
+                              tc_wait(&a_empty[h], static_cast<uint32_t>(cc - 1) & 1u, abort_flag))) {
+                ok = false;
+                break;
+              }
+            }
+            if (live) {
+              if (half == 0) tc_fence_after();
+#pragma unroll
+              for (int s = 0; s < S; ++s)
+                tc_st16(tmem + lane_base + kACol + 32u * (mi0 + s) + 16u * half, ev[s]);
             }
           }
-          }
-          hand_over();  // the previous chunk
-          // this chunk's buffer is free once the MMAs of chunk cc - 2 have completed (also waited
-          // for when nothing is stored: the arrivals on a_full must not run ahead of the MMA thread
-          // by more than one phase)
-          if (cc >= 2 && !__all_sync(0xffffffffu, tc_wait(&a_empty[buf], static_cast<uint32_t>((cc >> 1) - 1) & 1u,
-                                                          abort_flag))) {
-            ok = false;
-            break;
-          }
-          if (live) {
-            tc_fence_after();
-#pragma unroll
-            for (int s = 0; s < S; ++s) tc_st16(tmem + lane_base + kACol + 128u * buf + 16u * (mi0 + s), ev[s]);
-            pending = buf;
-          } else {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_full[buf]);
-          }
+          if (!ok) break;
+          if (live) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&a_full[h]);
         }
         if (!ok) break;
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[stage]);  // the record planes of this tile are no longer read
       }
       if (!ok) break;
-      hand_over();
       // segment end: the accumulators of this thread's sources
-      if (!__all_sync(0xffffffffu, tc_wait(d_full, static_cast<uint32_t>(seg) & 1u, abort_flag))) {
+      if (!__all_sync(0xffffffffu, tc_wait(&d_full[h], static_cast<uint32_t>(seg) & 1u, abort_flag))) {
         ok = false;
         break;
       }
@@ -481,7 +475,7 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(d_empty);
+      if (lane == 0) mbar_arrive(&d_empty[h]);
       ++seg;
     }
     if (!ok) {
@@ -494,7 +488,7 @@ __global__ void __launch_bounds__((CW + 2) * 32, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == CW + 1) {
+  if (warp == kMmaWarp0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
@@ -549,14 +543,14 @@ cudaError_t launch_features(const BatchPlan& p, const float* rec, const float4* 
 }
 
 namespace {
-template <int MODE, int CW>
+template <int MODE>
 cudaError_t launch_tc_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, const float* feat,
                         const float* ls_n, float* part, int* status, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(estep_tc_kernel<MODE, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(estep_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kTcSmem));
   if (e != cudaSuccess) return e;
-  estep_tc_kernel<MODE, CW><<<p.g.grid, (CW + 2) * 32, kTcSmem, s>>>(xs, rec, feat, d.st, ls_n, part, d.tab,
-                                                                       d.done_count, status, p.g);
+  estep_tc_kernel<MODE><<<p.g.grid, kTcThreads, kTcSmem, s>>>(xs, rec, feat, d.st, ls_n, part, d.tab, d.done_count,
+                                                              status, p.g);
   return cudaGetLastError();
 }
 }  // namespace
@@ -564,8 +558,8 @@ cudaError_t launch_tc_t(const BatchPlan& p, const Dev& d, const float4* xs, cons
 cudaError_t launch_estep_tc(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, const float* feat,
                             int mode, const float* ls_n, float* part, int* status, cudaStream_t s) {
   if (p.g.SB != kTcSB) return cudaErrorInvalidValue;
-  if (mode) return launch_tc_t<1, kTcCW>(p, d, xs, rec, feat, ls_n, part, status, s);
-  return launch_tc_t<0, kTcCW>(p, d, xs, rec, feat, nullptr, part, status, s);
+  if (mode) return launch_tc_t<1>(p, d, xs, rec, feat, ls_n, part, status, s);
+  return launch_tc_t<0>(p, d, xs, rec, feat, nullptr, part, status, s);
 }
 
 }  // namespace lsg
