@@ -17,26 +17,32 @@
 // features are split hi + lo in TF32 (about 21 significant bits).  Relative to
 // the FP32 kernel, per-source normalised moments move by at most ~2^-9.
 //
-// CTA (one per SM; all 512 TMEM columns):
-//   warps 0-7  compute.  Thread (w, l) owns sources w*128 + s*32 + l (s = 0..3)
-//              of the source block; source s of warp w is row 32 (w % 4) + l
-//              of matrix mi = 4 (w / 4) + s (a warp reaches only its quarter
-//              of the TMEM lanes).  For every chunk of 16 targets it writes
-//              its 4 x 16 exponentials into TMEM (the A operand).
-//   warp 8     producer: bulk copies (cp.async.bulk) of each target tile:
+// CTA (one per SM; all 512 TMEM columns; 1024 sources = 8 matrices of 128 rows):
+//   warps 0-15 compute, 2 sources per thread.  Thread (w, l) owns sources
+//              w*64 + s*32 + l (s = 0, 1) of the source block; source s of
+//              warp w is row 32 (w % 4) + l of matrix mi = 2 (w / 4) + s (a
+//              warp reaches only its quarter of the TMEM lanes).  Warps 0-7
+//              form half 0 (matrices 0-3), warps 8-15 half 1 (matrices 4-7);
+//              the halves never wait for each other.  For every chunk of 32
+//              targets a thread writes its 2 x 32 exponentials into TMEM (the
+//              A operand), 16 at a time.
+//   warps 16, 17  MMA issuer of half 0 (also TMEM owner) and of half 1: one
+//              thread each issues the MMAs of its 4 matrices (M = 128 sources,
+//              N = 32 features, K = 8 targets per instruction) and commits.
+//   warp 18    producer: bulk copies (cp.async.bulk) of each target tile:
 //              16 KB of features in the canonical K-major core-matrix layout
 //              (the B operand) and the 7 record planes q needs.
-//   warp 9     TMEM owner; one thread issues the MMAs (M = 128 sources,
-//              N = 32 features, K = 8 targets per instruction) and commits.
-// TMEM columns: accumulators D of matrix mi at 32 mi (F32), A chunk buffers
-// (two, 16 TF32 columns per matrix) at 256 + 128 buf + 16 mi.
+// TMEM columns: accumulators D of matrix mi at 32 mi (F32), the A chunk buffer
+// of matrix mi (32 TF32 columns) at 256 + 32 mi.
 // mbarriers (every wait is bounded; a timeout sets ETIMEOUT, lets the copies
 // and MMAs in flight finish, frees TMEM and returns):
-//   full[stage]  tile landed           empty[stage]  8 compute warps + MMA commit
-//   a_full[buf]  8 warps wrote A       a_empty[buf]  MMA commit (A consumed)
-//   d_full       segment's MMAs done   d_empty       8 warps read D
+//   full[stage]  tile landed              empty[stage]  16 compute warps + both MMA commits
+//   a_full[h]    8 warps wrote A of half h   a_empty[h]  MMA commit (A of half h consumed)
+//   d_full[h]    segment's MMAs of half h done   d_empty[h]  8 warps read D of half h
+// The MMAs of chunk c run while the compute warps compute the first 16 targets
+// of chunk c + 1; the buffer is reused only after they complete.
 // Segments (FP32 flush points) and partial slots are those of the FP32 kernel
-// with 4 sources per thread, so the combine is shared.
+// with 4 sources per thread (source blocks of 1024), so the combine is shared.
 #include <math.h>
 
 #include "internal.cuh"
