@@ -116,35 +116,35 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 }
 
 // Bounded wait that also gives up once another role of the CTA has aborted.  The
-// producer and MMA roles poll with a back-off of `sleep_ns` between attempts, so
-// that a waiting role takes few issue slots from the compute warps of its
-// scheduler (they have a chunk or more of slack); the compute warps poll without one.
-#ifndef LSG_TC_PRODUCER_SLEEP
-#define LSG_TC_PRODUCER_SLEEP 0
-#endif
-#ifndef LSG_TC_MMA_SLEEP
-#define LSG_TC_MMA_SLEEP 0
-#endif
-constexpr unsigned kProducerSleepNs = LSG_TC_PRODUCER_SLEEP;
-constexpr unsigned kMmaSleepNs = LSG_TC_MMA_SLEEP;
+// producer and MMA threads (`idle_role`) pass a suspend-time hint to try_wait, so that
+// while they wait they take fewer issue slots from the compute warps of their
+// schedulers; the compute warps poll without one.
+constexpr uint32_t kSuspendHintNs = 20000;
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag,
-                                        unsigned sleep_ns = 0) {
+                                        bool idle_role = false) {
   const uint32_t a = smem_addr(bar);
   long long t0 = -1;
   while (true) {
     uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
+    if (idle_role) {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+          : "=r"(ok)
+          : "r"(a), "r"(parity), "r"(kSuspendHintNs)
+          : "memory");
+    } else {
+      asm volatile(
+          "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+          : "=r"(ok)
+          : "r"(a), "r"(parity)
+          : "memory");
+    }
     if (ok) return true;
     if (*abort_flag) return false;
     const long long now = clock64();
     if (t0 < 0) t0 = now;
     if (now - t0 > kWaitBudgetCycles) return false;
-    if (sleep_ns) __nanosleep(sleep_ns);
   }
 }
 
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < n_units; ++i) {
         const int stage = i % kTcStages;
         if (i >= kTcStages &&
-            !tc_wait(&empty[stage], static_cast<uint32_t>(i / kTcStages - 1) & 1u, abort_flag, kProducerSleepNs)) {
+            !tc_wait(&empty[stage], static_cast<uint32_t>(i / kTcStages - 1) & 1u, abort_flag, true)) {
           atomicOr(status, kStatusTimeout);
           *abort_flag = 1;
           break;
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (seg_end > unit_off[b + 1]) seg_end = unit_off[b + 1];
         if (seg_end > u1) seg_end = u1;
         // the compute warps of this half have read the previous segment's accumulators
-        if (seg > 0 && !tc_wait(&d_empty[h], static_cast<uint32_t>(seg - 1) & 1u, abort_flag, kMmaSleepNs)) {
+        if (seg > 0 && !tc_wait(&d_empty[h], static_cast<uint32_t>(seg - 1) & 1u, abort_flag, true)) {
           ok = false;
           break;
         }
@@ -308,13 +308,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         bool first = true;
         for (; u < seg_end; ++u, ++i) {
           const int stage = i % kTcStages;
-          if (!tc_wait(&full[stage], static_cast<uint32_t>(i / kTcStages) & 1u, abort_flag, kMmaSleepNs)) {
+          if (!tc_wait(&full[stage], static_cast<uint32_t>(i / kTcStages) & 1u, abort_flag, true)) {
             ok = false;
             break;
           }
           const uint32_t fb = smem_addr(smem_raw + stage * kStageBytes);
           for (int c = 0; c < kChunks; ++c, ++cc) {
-            if (!tc_wait(&a_full[h], static_cast<uint32_t>(cc) & 1u, abort_flag, kMmaSleepNs)) {
+            if (!tc_wait(&a_full[h], static_cast<uint32_t>(cc) & 1u, abort_flag, true)) {
               ok = false;
               break;
             }
