@@ -208,7 +208,7 @@ class ClockSampler:
 def kernel_source_hash(precision=0):
     """sha256 over the sources that define the E-step kernel (its file and its copy pipeline)."""
     h = hashlib.sha256()
-    for name in (("estep_tc.cu",) if precision == 2 else ("estep.cu",)) + ("pipeline.cuh",):
+    for name in (("estep_tc.cu",) if precision >= 2 else ("estep.cu",)) + ("pipeline.cuh",):
         with open(os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -217,7 +217,7 @@ def kernel_source_hash(precision=0):
 def profile_traffic(precision=0, workload="rgbd20k"):
     """DRAM traffic per E-step launch from the committed ncu summary, if it was taken
     on the current kernel source and on this workload (null otherwise)."""
-    if workload != "rgbd20k":
+    if workload != "rgbd20k" or precision not in (0, 2):
         return None
     name = "estep_tc_rgbd20k_traffic.json" if precision == 2 else "estep_rgbd20k_traffic.json"
     path = os.path.join(ROOT, "profiles", name)
@@ -405,7 +405,7 @@ def run_ours(args):
     ex2_rate = EX2_PER_PAIR * N * M / t_launch
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": profile_traffic(args.precision, args.workload),
-            "kernel": "estep_tc_kernel" if args.precision == 2 else "estep_kernel",
+            "kernel": "estep_tc_kernel" if args.precision >= 2 else "estep_kernel",
             "ms_per_launch": round(t_launch * 1e3, 5),
             "pairs_per_s_per_launch": N * M / t_launch,
             "counted": f"{ops} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, N*M pairs per launch",
