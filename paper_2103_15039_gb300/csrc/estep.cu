@@ -617,7 +617,7 @@ cudaError_t launch_posteriors(const float4* xs, const float* rec, const EmState*
 }
 
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
-                     int S_override) {
+                     int S_override, int seg_cap) {
   BatchPlan p{};
   Geo& g = p.g;
   const int P = static_cast<int>(N.size());
@@ -663,7 +663,7 @@ BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long lon
   }
   g.S = chosen;
   g.SB = warps_of(chosen) * 32 * chosen;
-  g.seg_cap = 64;
+  g.seg_cap = seg_cap;
   // pair tables
   std::vector<int> blk_off(P + 1, 0), tile_off(P + 1, 0);
   g.max_blocks = 0;

@@ -174,9 +174,11 @@ struct BatchPlan {
 };
 
 // Plan a batch (sizes N[i], M[i]); S_override in {1, 2, 4} forces the
-// sources per thread, 0 chooses.
+// sources per thread, 0 chooses.  seg_cap: target tiles a CTA sums into one
+// partial slot at most (the length of an FP32 accumulation run).
+constexpr int kSegCap = 64;
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
-                     int S_override);
+                     int S_override, int seg_cap = kSegCap);
 size_t estep_partial_floats(const Geo& g);
 
 // Device pointers of a batch.

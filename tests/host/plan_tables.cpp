@@ -18,8 +18,10 @@ int failures = 0;
     if (!(cond) && failures++ < 20) std::printf("failed: %s (line %d)\n", #cond, __LINE__); \
   } while (0)
 
-void check_plan(const std::vector<long long>& N, const std::vector<long long>& M, int sms, int S) {
-  const lsg::BatchPlan plan = lsg::plan_batch(N, M, sms, S);
+void check_plan(const std::vector<long long>& N, const std::vector<long long>& M, int sms, int S,
+                int seg_cap = lsg::kSegCap) {
+  const lsg::BatchPlan plan = lsg::plan_batch(N, M, sms, S, seg_cap);
+  EXPECT(plan.g.seg_cap == seg_cap);
   const lsg::Geo& g = plan.g;
   const int* t = plan.tab.data();
   const int P = g.P;
@@ -131,6 +133,19 @@ int main() {
       cases += 3;
     }
   }
+  // 4 sources per thread (the tensor-core kernel's tile) with shorter segments
+  for (int trial = 0; trial < 40; ++trial) {
+    const int P = 1 + static_cast<int>(rng() % 300);
+    std::vector<long long> N(P), M(P);
+    for (int i = 0; i < P; ++i) {
+      N[i] = 1 + static_cast<long long>(rng() % 30000);
+      M[i] = 1 + static_cast<long long>(rng() % 30000);
+    }
+    check_plan(N, M, 152, 4, 16);
+    ++cases;
+  }
+  check_plan({500000}, {500000}, 152, 4, 16);
+  ++cases;
   std::printf("%d plans checked, %d failures\n", cases, failures);
   return failures != 0;
 }
