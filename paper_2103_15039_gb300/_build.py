@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "liblsgcpd.so")
-SOURCES = ["estep.cu", "estep_tc.cu", "mstep.cu", "prep.cu", "knn_grid.cu", "api.cu", "noalloc.cu", "diag.cu"]
+SOURCES = ["estep.cu", "estep_tc.cu", "plan.cu", "mstep.cu", "prep.cu", "knn_grid.cu", "api.cu", "noalloc.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"]

@@ -180,6 +180,10 @@ constexpr int kSegCap = 64;
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
                      int S_override, int seg_cap = kSegCap);
 size_t estep_partial_floats(const Geo& g);
+// Resident CTAs per SM and warps per CTA of the FP32 E-step kernel with S sources per thread.
+int estep_resident_ctas(int S);
+int estep_warps(int S);
+size_t estep_smem_bytes();  // dynamic shared memory of the FP32 E-step kernel
 
 // Device pointers of a batch.
 struct Dev {
