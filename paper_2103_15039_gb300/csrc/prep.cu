@@ -366,13 +366,13 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
       cz[j] = make_float2(-c.z, -c.z);
     }
     __syncthreads();
-    // four candidates per step: independent distance chains, one branch per query
-    // unless a candidate passes (then the four are inserted in index order)
+    // eight candidates per step: independent distance chains, one branch per query
+    // unless a candidate passes (then the eight are inserted in index order)
     int j = 0;
-    for (; j + 4 <= cnt; j += 4) {
-      float2 d[4];
+    for (; j + 8 <= cnt; j += 8) {
+      float2 d[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const float4 a = cxy[j + u];
         const float2 dx = __fadd2_rn(px, make_float2(a.x, a.y));
         const float2 dy = __fadd2_rn(py, make_float2(a.z, a.w));
@@ -380,14 +380,14 @@ __global__ void __launch_bounds__(kKnnThreads) knn_partial_kernel(const float4* 
         d[u] = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
       }
       const int ci = static_cast<int>(base + j);
-      if (fminf(fminf(d[0].x, d[1].x), fminf(d[2].x, d[3].x)) < thr0) {
+      if (fminf(fminf(fminf(d[0].x, d[1].x), fminf(d[2].x, d[3].x)), fminf(fminf(d[4].x, d[5].x), fminf(d[6].x, d[7].x))) < thr0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
           if (d[u].x < thr0) knn_insert<KMAX>(bd0, bi0, thr0, k, d[u].x, ci + u, cap0);
       }
-      if (fminf(fminf(d[0].y, d[1].y), fminf(d[2].y, d[3].y)) < thr1) {
+      if (fminf(fminf(fminf(d[0].y, d[1].y), fminf(d[2].y, d[3].y)), fminf(fminf(d[4].y, d[5].y), fminf(d[6].y, d[7].y))) < thr1) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
           if (d[u].y < thr1) knn_insert<KMAX>(bd1, bi1, thr1, k, d[u].y, ci + u, cap1);
       }
     }
