@@ -246,6 +246,18 @@ lsgcpd_status lsgcpd_set_autotune(lsgcpd_ctx* ctx, int enable);
  * sources per thread (0 where not measured).  Host memory. */
 lsgcpd_status lsgcpd_plan_info(const lsgcpd_ctx* ctx, int32_t info[4], double tune_ms[3]);
 
+/* Persistent autotune cache (no counterpart in the paper).  save writes the
+ * context's measured choices (problem shape -> sources per thread and the three
+ * trial times) to a text file at `path` (UTF-8, one entry per line after a
+ * header line), keyed by this device's name and SM count; EINVAL if the file
+ * cannot be written.  load reads such a file and adds the entries written on
+ * a device with the same name and SM count (others, and malformed lines, are
+ * skipped), so that later calls with those shapes skip the trial launches;
+ * *count (may be NULL) receives the number of entries added; EINVAL if the
+ * file cannot be read or its header is not that of this format. */
+lsgcpd_status lsgcpd_autotune_save(const lsgcpd_ctx* ctx, const char* path);
+lsgcpd_status lsgcpd_autotune_load(lsgcpd_ctx* ctx, const char* path, int32_t* count);
+
 /* Diagnostic of the failure path of the E step's copy pipeline (no
  * counterpart in the paper): one kernel waits, with the same bounded wait the
  * E step uses on its target-tile barriers, on a shared-memory barrier that

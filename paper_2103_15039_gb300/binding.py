@@ -91,6 +91,10 @@ def lib():
         L.lsgcpd_set_autotune.restype = C.c_int
         L.lsgcpd_plan_info.argtypes = [vp, C.POINTER(C.c_int32), dp]
         L.lsgcpd_plan_info.restype = C.c_int
+        L.lsgcpd_autotune_save.argtypes = [vp, C.c_char_p]
+        L.lsgcpd_autotune_save.restype = C.c_int
+        L.lsgcpd_autotune_load.argtypes = [vp, C.c_char_p, C.POINTER(C.c_int32)]
+        L.lsgcpd_autotune_load.restype = C.c_int
         L.lsgcpd_estep_noalloc.argtypes = [fp, i64, fp, fp, fp, i64, C.POINTER(Params), dp, dp, C.c_double,
                                            C.c_double, dp, fp, vp]
         L.lsgcpd_estep_noalloc.restype = C.c_int
@@ -378,6 +382,17 @@ def lsgcpd_set_autotune(ctx, enable):
     _check(ctx, lib().lsgcpd_set_autotune(ctx, 1 if enable else 0))
 
 
+def lsgcpd_autotune_save(ctx, path):
+    _check(ctx, lib().lsgcpd_autotune_save(ctx, str(path).encode()))
+
+
+def lsgcpd_autotune_load(ctx, path):
+    """Entries of a saved autotune file (this device) added to the context; returns their count."""
+    n = C.c_int32(0)
+    _check(ctx, lib().lsgcpd_autotune_load(ctx, str(path).encode(), C.byref(n)))
+    return int(n.value)
+
+
 def lsgcpd_plan_info(ctx):
     info = np.zeros(4, dtype=np.int32)
     ms = np.zeros(3)
@@ -444,6 +459,12 @@ class Context:
 
     def plan_info(self):
         return lsgcpd_plan_info(self.handle)
+
+    def autotune_save(self, path):
+        lsgcpd_autotune_save(self.handle, path)
+
+    def autotune_load(self, path):
+        return lsgcpd_autotune_load(self.handle, path)
 
     def set_timing(self, enable):
         lsgcpd_set_timing(self.handle, enable)

@@ -3,7 +3,9 @@
 // and the conversions between the centred working frame and the caller's frame.
 // A single registration is a batch of one pair.
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -515,12 +517,45 @@ lsgcpd_status stage(lsgcpd_ctx* c, const float* X, const float* Y, const std::ve
 
 // One or more registrations: X and Y are the concatenated clouds (host or
 // device), sizes N[i], M[i].  Results per pair in the caller's frame.
+// NVTX range over a host phase (a no-op unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// LSGCPD_LOG=1: print every pair's per-iteration trace to stderr after a registration.
+bool log_enabled() {
+  const char* v = getenv("LSGCPD_LOG");
+  return v && v[0] && strcmp(v, "0") != 0;
+}
+
+void print_trace(const double* trace, int P, int iters, const std::vector<EmState>& hs) {
+  for (int i = 0; i < P; ++i)
+    for (int it = 0; it < hs[i].iter && it < iters; ++it) {
+      const double* r = trace + (static_cast<size_t>(i) * iters + it) * LSGCPD_TRACE_WIDTH;
+      fprintf(stderr,
+              "lsgcpd pair %d iter %d: sigma2 %.9g N_P %.9g Q %.9g newton %d damped %d motion %.3g nll %.12g "
+              "outlier mass %.6g\n",
+              i, it, r[0], r[1], r[2], static_cast<int>(r[3]), static_cast<int>(r[4]), r[5], r[6], r[7]);
+    }
+}
+
 lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N_in,
                                const std::vector<long long>& M_in, const lsgcpd_params* p, double* R_out,
                                double* t_out, double* sigma2_out, int32_t* iters_out, int32_t* mode_out,
                                double* trace, void* stream) {
+  NvtxRange range_all("lsgcpd registration");
   const int P = static_cast<int>(N_in.size());
   const int k = p->knn_k;
+  // with LSGCPD_LOG the trace is recorded into a host buffer of our own if the caller did not ask for it
+  std::vector<double> log_trace;
+  const bool log = log_enabled() && p->max_iters > 0;
+  if (log && !trace) {
+    log_trace.assign(static_cast<size_t>(P) * p->max_iters * LSGCPD_TRACE_WIDTH, 0.0);
+    trace = log_trace.data();
+  }
   LSG_CUDA(enter(c, stream), "stream");
   cudaStream_t s = c->stream;
   const bool xd = is_device_ptr(X), yd = is_device_ptr(Y);
@@ -530,7 +565,11 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     LSG_CUDA(cudaEventRecord(c->t_begin, s), "event");
   }
   Staged in;
-  lsgcpd_status rs = stage(c, X, Y, N_in, M_in, p, xd, yd, &in);
+  lsgcpd_status rs;
+  {
+    NvtxRange r("lsgcpd stage inputs");
+    rs = stage(c, X, Y, N_in, M_in, p, xd, yd, &in);
+  }
   if (rs != LSGCPD_OK) {
     leave(c, stream);
     return rs;
@@ -694,6 +733,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       }
       c->gkey = key;
     }
+    NvtxRange r("lsgcpd EM loop (graph)");
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
     launches += static_cast<int64_t>(iters) * (mode ? 7 : 5);
   }
@@ -706,6 +746,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
              "copy trace");
   LSG_CUDA(cudaStreamSynchronize(s), "sync");
   LSG_CUDA(leave(c, stream), "stream");
+  if (log && iters > 0) print_trace(trace, P, iters, hs);
   c->launches = launches;
   c->h2d_bytes = in.h2d +
                  static_cast<int64_t>(sizeof(int) * plan.tab.size() + sizeof(long long) * plan.off64.size());
@@ -842,6 +883,85 @@ lsgcpd_status lsgcpd_set_timing(lsgcpd_ctx* c, int enable) {
 lsgcpd_status lsgcpd_set_autotune(lsgcpd_ctx* c, int enable) {
   if (!c) return LSGCPD_EINVAL;
   c->autotune = enable ? 1 : 0;
+  return LSGCPD_OK;
+}
+
+namespace {
+// Key of this context's device in the autotune file: its name (spaces as '_') and SM count.
+std::string device_key(const lsgcpd_ctx* c) {
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, c->device) == cudaSuccess) name = prop.name;
+  else cudaGetLastError();
+  for (char& ch : name)
+    if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+  return name + ":" + std::to_string(c->num_sms);
+}
+const char kTuneHeader[] = "lsgcpd-autotune 1";
+}  // namespace
+
+lsgcpd_status lsgcpd_autotune_save(const lsgcpd_ctx* c, const char* path) {
+  if (!c || !path) return LSGCPD_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return LSGCPD_EINVAL;
+  const std::string key = device_key(c);
+  fprintf(f, "%s\n", kTuneHeader);
+  // line: device-key S ms4 ms2 ms1 n_sizes sizes...
+  for (const auto& t : c->tuned) {
+    fprintf(f, "%s %d %.9g %.9g %.9g %zu", key.c_str(), t.S, t.ms[0], t.ms[1], t.ms[2], t.sizes.size());
+    for (long long v : t.sizes) fprintf(f, " %lld", v);
+    fprintf(f, "\n");
+  }
+  const bool ok = fclose(f) == 0;
+  return ok ? LSGCPD_OK : LSGCPD_EINVAL;
+}
+
+lsgcpd_status lsgcpd_autotune_load(lsgcpd_ctx* c, const char* path, int32_t* count) {
+  if (!c || !path) return LSGCPD_EINVAL;
+  if (count) *count = 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(c, LSGCPD_EINVAL, "autotune file cannot be read");
+  const std::string key = device_key(c);
+  std::vector<char> line(1 << 20);
+  int added = 0;
+  bool header = false;
+  while (fgets(line.data(), static_cast<int>(line.size()), f)) {
+    if (!header) {
+      header = strncmp(line.data(), kTuneHeader, sizeof(kTuneHeader) - 1) == 0;
+      if (!header) break;
+      continue;
+    }
+    char dev[256];
+    int S = 0, used = 0;
+    size_t n = 0;
+    double ms[3];
+    if (sscanf(line.data(), "%255s %d %lf %lf %lf %zu%n", dev, &S, &ms[0], &ms[1], &ms[2], &n, &used) != 6) continue;
+    if (key != dev || (S != 1 && S != 2 && S != 4) || n == 0 || n % 2 != 0 || n > 2 * LSGCPD_MAX_PAIRS) continue;
+    lsgcpd_ctx::Tuned t;
+    t.S = S;
+    for (int i = 0; i < 3; ++i) t.ms[i] = ms[i];
+    const char* q = line.data() + used;
+    bool good = true;
+    for (size_t i = 0; i < n && good; ++i) {
+      long long v = 0;
+      int u = 0;
+      good = sscanf(q, "%lld%n", &v, &u) == 1 && v > 0;
+      q += u;
+      t.sizes.push_back(v);
+    }
+    if (!good) continue;
+    bool dup = false;
+    for (auto& e : c->tuned)
+      if (e.sizes == t.sizes) {
+        e = t;
+        dup = true;
+      }
+    if (!dup) c->tuned.push_back(t);
+    ++added;
+  }
+  fclose(f);
+  if (!header) return fail(c, LSGCPD_EINVAL, "not an autotune file");
+  if (count) *count = added;
   return LSGCPD_OK;
 }
 

@@ -78,3 +78,42 @@ def test_autotuned_batch_matches_untuned():
             assert np.linalg.norm(a["t"][i] - b["t"][i]) / _diag(c["Y"]) < 1e-5
     finally:
         ctx.close()
+
+
+def test_autotune_cache_persists_across_contexts(tmp_path):
+    """A saved cache makes a new context reuse the measured tile: no trial launches (fewer
+    launches on the first call) and the same plan, hence the same bits."""
+    c = synth.sphere_plane_pair(seed=57, n=3100, m=2600)
+    p = binding.default_params(max_iters=5)
+    path = tmp_path / "tune.txt"
+    a_ctx = binding.Context(0, 4096, 4096)
+    try:
+        a_ctx.set_timing(True)
+        a = a_ctx.register(c["X"], c["Y"], p)
+        a_launches = a_ctx.last_timing()["launches"]
+        a_info = a_ctx.plan_info()
+        a_ctx.autotune_save(path)
+    finally:
+        a_ctx.close()
+    text = path.read_text().splitlines()
+    assert text[0] == "lsgcpd-autotune 1" and len(text) == 2
+    b_ctx = binding.Context(0, 4096, 4096)
+    try:
+        assert b_ctx.autotune_load(path) == 1
+        b_ctx.set_timing(True)
+        b = b_ctx.register(c["X"], c["Y"], p)
+        b_info = b_ctx.plan_info()
+        assert b_info["tuned"] and b_info["sources_per_thread"] == a_info["sources_per_thread"]
+        assert b_info["tune_ms"] == a_info["tune_ms"]
+        assert b_ctx.last_timing()["launches"] < a_launches  # no trial launches
+        np.testing.assert_array_equal(a["R"], b["R"])
+        # another device's entries and malformed lines are skipped; a file of another format is refused
+        other = tmp_path / "other.txt"
+        other.write_text("lsgcpd-autotune 1\nSomeOtherGPU:10 2 1 1 1 2 3100 2600\ngarbage line\n")
+        assert b_ctx.autotune_load(other) == 0
+        bad = tmp_path / "bad.txt"
+        bad.write_text("not a cache\n")
+        with pytest.raises(binding.LsgcpdError):
+            b_ctx.autotune_load(bad)
+    finally:
+        b_ctx.close()

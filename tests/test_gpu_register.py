@@ -115,3 +115,37 @@ def test_timing_enabled_calls_report_kernel_times_and_leave_no_error(ctx):
         np.testing.assert_array_equal(a["R"], b["R"])
     finally:
         ctx.set_timing(False)
+
+
+def test_resume_from_a_saved_state_continues_the_same_run(ctx):
+    """Checkpoint / resume: the EM state is (R, t, sigma^2).  25 iterations, then 25 more
+    started from the first run's result (init_R, init_t, sigma2_init), end where 50
+    iterations in one call end (the pose passes once through the caller's frame in FP64)."""
+    c = synth.sphere_plane_pair(seed=71, n=1100, m=1000)
+    full = ctx.register(c["X"], c["Y"], binding.default_params(max_iters=50))
+    first = ctx.register(c["X"], c["Y"], binding.default_params(max_iters=25))
+    second = ctx.register(c["X"], c["Y"], binding.default_params(max_iters=25, init_R=first["R"], init_t=first["t"],
+                                                                  sigma2_init=first["sigma2"]))
+    assert oracle.rotation_error(second["R"], full["R"]) < 1e-9
+    assert np.linalg.norm(second["t"] - full["t"]) / _diag(c["Y"]) < 1e-9
+    assert second["sigma2"] == pytest.approx(full["sigma2"], rel=1e-9)
+
+
+def test_log_environment_variable_prints_the_trace(tmp_path):
+    """LSGCPD_LOG=1 prints one line per pair and iteration to stderr."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2103_15039_gb300 import binding, synth\n"
+            "c = synth.sphere_plane_pair(n=300, m=300)\n"
+            "ctx = binding.Context(0, 300, 300)\n"
+            "r = ctx.register(c['X'], c['Y'], binding.default_params(max_iters=7))\n"
+            "print('iters', r['iters'])\n" % root)
+    env = dict(os.environ, LSGCPD_LOG="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stderr.splitlines() if ln.startswith("lsgcpd pair 0 iter ")]
+    assert len(lines) == 7 and "sigma2" in lines[0] and "newton" in lines[0]
+    assert "iters 7" in out.stdout
