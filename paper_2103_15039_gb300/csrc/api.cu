@@ -908,7 +908,7 @@ lsgcpd_status lsgcpd_autotune_save(const lsgcpd_ctx* c, const char* path) {
   fprintf(f, "%s\n", kTuneHeader);
   // line: device-key S ms4 ms2 ms1 n_sizes sizes...
   for (const auto& t : c->tuned) {
-    fprintf(f, "%s %d %.9g %.9g %.9g %zu", key.c_str(), t.S, t.ms[0], t.ms[1], t.ms[2], t.sizes.size());
+    fprintf(f, "%s %d %.17g %.17g %.17g %zu", key.c_str(), t.S, t.ms[0], t.ms[1], t.ms[2], t.sizes.size());
     for (long long v : t.sizes) fprintf(f, " %lld", v);
     fprintf(f, "\n");
   }
