@@ -305,19 +305,31 @@ def errors_vs(got, ref, diag):
 
 
 def time_registrations(ctx, Xd, Yd, p, steps, flush, stream):
-    """Device-resident registrations timed with CUDA events (L2 flushed before each)."""
+    """Device-resident registrations timed with CUDA events (L2 flushed before each): the step
+    time without the library's per-kernel events, then the E step's per-launch time from a
+    pass with them."""
     import torch
-    step_ms, estep_ms, got = [], [], None
-    for _ in range(steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        got = ctx.register(Xd, Yd, p)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        estep_ms.append(ctx.last_timing()["ms_estep"])
+
+    def run(timing):
+        ctx.set_timing(timing)
+        ctx.register(Xd, Yd, p)
+        step_ms, estep_ms, got = [], [], None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            got = ctx.register(Xd, Yd, p)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            if timing:
+                estep_ms.append(ctx.last_timing()["ms_estep"])
+        return got, step_ms, estep_ms
+
+    got, step_ms, _ = run(False)
+    _, _, estep_ms = run(True)
+    ctx.set_timing(False)
     return got, statistics.mean(step_ms), statistics.mean(estep_ms) / got["iters"]
 
 
@@ -349,16 +361,19 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ctx.set_timing(True)
+    # The library's per-kernel CUDA events are event nodes in the captured EM graph (four per
+    # iteration, a few microseconds each), so the headline pass runs without them and a second
+    # timed pass with them gives the E step's per-launch time and the device breakdown.
+    ctx.set_timing(False)
     settle(lambda: ctx.register(Xd, Yd, p))
     for _ in range(max(args.warmup, 0)):
         got = ctx.register(Xd, Yd, p)
         ctx.register(Xh, Yh, p)
 
-    # --- device-resident timed region ---
+    # --- device-resident timed region (the headline) ---
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, estep_ms, launches = [], [], 0
+    step_ms, launches = [], 0
     barrier()
     for _ in range(args.steps):
         flush.zero_()
@@ -369,14 +384,33 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        tm = ctx.last_timing()
-        estep_ms.append(tm["ms_estep"])
-        launches += tm["launches"]
+        launches += ctx.last_timing()["launches"]
     barrier()
     clk = clocks.stop()
     iters_run = got["iters"]
-    # device-time breakdown of the last timed step (CUDA events recorded by the library)
+
+    # --- kernel-timing pass: the same steps with the library's per-kernel events ---
+    ctx.set_timing(True)
+    for _ in range(max(args.warmup, 1)):
+        ctx.register(Xd, Yd, p)
+    barrier()
+    estep_ms, timed_step_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.register(Xd, Yd, p)
+        e1.record(stream)
+        e1.synchronize()
+        timed_step_ms.append(e0.elapsed_time(e1))
+        tm = ctx.last_timing()
+        estep_ms.append(tm["ms_estep"])
+    barrier()
+    ctx.set_timing(False)
+    # device-time breakdown of the last step of that pass (CUDA events recorded by the library)
     breakdown = {k: round(tm[k], 4) for k in ("ms_total", "ms_prep", "ms_estep", "ms_combine", "ms_mstep")}
+    breakdown["ms_per_step_with_kernel_events"] = round(statistics.mean(timed_step_ms), 4)
 
     # --- end-to-end: pinned host inputs, copies inside the C call, result on the host ---
     e2e_s = []
@@ -398,6 +432,7 @@ def run_ours(args):
     t_launch = statistics.mean(estep_ms) / iters_run / 1e3
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12  # FP32-pipe Top/s
+    # (per-launch time from the kernel-timing pass, on the stream the kernel runs on)
     # the tensor-core variant is measured against the FP32-pipe work it keeps (the moment sums
     # run on tcgen05 at ~11 % of the tensor pipe)
     ops = TC_FP32_OPS_PER_PAIR if args.precision == 2 else FLOPS_PER_PAIR
@@ -407,6 +442,8 @@ def run_ours(args):
             "frac": round(achieved / peak, 4), "traffic": profile_traffic(args.precision, args.workload),
             "kernel": "estep_tc_kernel" if args.precision >= 2 else "estep_kernel",
             "ms_per_launch": round(t_launch * 1e3, 5),
+            "launch_timing": "CUDA events around every E-step launch, recorded as nodes of the captured EM graph "
+                             "on its stream, in a second timed pass (the headline pass runs without them)",
             "pairs_per_s_per_launch": N * M / t_launch,
             "counted": f"{ops} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, N*M pairs per launch",
             "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)",
@@ -492,14 +529,16 @@ def run_batch(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ctx.set_timing(True)
+    # headline pass without the library's per-kernel events (graph event nodes cost a few
+    # microseconds each), then a kernel-timing pass with them for the roofline
+    ctx.set_timing(False)
     settle(lambda: ctx.register_batch(Xd, n_off, Yd, m_off, p))
     for _ in range(max(args.warmup, 0)):
         got = ctx.register_batch(Xd, n_off, Yd, m_off, p)
         ctx.register_batch(Xh, n_off, Yh, m_off, p)
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, estep_ms, launches = [], [], 0
+    step_ms, launches = [], 0
     barrier()
     for _ in range(args.steps):
         flush.zero_()
@@ -510,11 +549,21 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        tm = ctx.last_timing()
-        estep_ms.append(tm["ms_estep"])
-        launches += tm["launches"]
+        launches += ctx.last_timing()["launches"]
     barrier()
     clk = clocks.stop()
+    ctx.set_timing(True)
+    ctx.register_batch(Xd, n_off, Yd, m_off, p)
+    barrier()
+    estep_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        ctx.register_batch(Xd, n_off, Yd, m_off, p)
+        torch.cuda.synchronize()
+        tm = ctx.last_timing()
+        estep_ms.append(tm["ms_estep"])
+    barrier()
+    ctx.set_timing(False)
     plan = plan_obj(ctx)
     iters_run = int(got["iters"].max())
     pairs_per_step = float((got["iters"].astype(np.float64) * nm).sum())
@@ -557,7 +606,9 @@ def run_batch(args):
     achieved = FLOPS_PER_PAIR * per_launch / t_launch / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "traffic": None, "kernel": "estep_kernel (whole batch per launch)",
-            "ms_per_launch": round(t_launch * 1e3, 5), "pairs_per_s_per_launch": per_launch / t_launch,
+            "ms_per_launch": round(t_launch * 1e3, 5),
+            "launch_timing": "CUDA events around every E-step launch, recorded as nodes of the captured EM graph "
+                             "on its stream, in a second timed pass (the headline pass runs without them)", "pairs_per_s_per_launch": per_launch / t_launch,
             "counted": f"{FLOPS_PER_PAIR} FP32-pipe ops + {EX2_PER_PAIR} EX2 per pair, sum N_i M_i pairs per launch",
             "peak_from": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {SM_MAX_MHZ_NOMINAL:.0f} MHz (max SM clock)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -593,7 +644,14 @@ def run_batch(args):
             e1.record(stream)
             e1.synchronize()
             t2.append(e0.elapsed_time(e1))
+        ctx.set_timing(True)  # E-step time per launch from a pass with the per-kernel events
+        ctx.register_batch(Xd, n_off, Yd, m_off, p2)
+        for _ in range(args.steps):
+            flush.zero_()
+            ctx.register_batch(Xd, n_off, Yd, m_off, p2)
+            torch.cuda.synchronize()
             est2.append(ctx.last_timing()["ms_estep"])
+        ctx.set_timing(False)
         barrier()
         ms2 = statistics.mean(t2)
         it2 = int(got2["iters"].max())
