@@ -517,6 +517,16 @@ lsgcpd_status stage(lsgcpd_ctx* c, const float* X, const float* Y, const std::ve
 
 // One or more registrations: X and Y are the concatenated clouds (host or
 // device), sizes N[i], M[i].  Results per pair in the caller's frame.
+}  // namespace
+
+namespace lsg {
+static thread_local bool t_pdl = false;
+void set_pdl(bool on) { t_pdl = on; }
+bool pdl_on() { return t_pdl; }
+}  // namespace lsg
+
+namespace {
+
 // NVTX range over a host phase (a no-op unless a profiler is attached).
 struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
@@ -701,6 +711,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       }
       cudaGraph_t gr = nullptr;
       LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+      set_pdl(true);  // consecutive kernels of the loop overlap their launch with the predecessor's tail
       cudaError_t ce = cudaSuccess;
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
@@ -720,6 +731,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
       }
+      set_pdl(false);
       cudaError_t ee = cudaStreamEndCapture(s, &gr);
       if (ce != cudaSuccess || ee != cudaSuccess) {
         if (gr) cudaGraphDestroy(gr);

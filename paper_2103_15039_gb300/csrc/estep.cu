@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
   float* tiles = reinterpret_cast<float*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + kStages * kTileBytes);
 
+  pdl_wait();
   if (*done_count >= g.P) return;
   const int* tile_off = tab + g.o_tile_off;
   const int* block_pair = tab + g.o_block_pair;
@@ -309,6 +310,8 @@ __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())
 __global__ void __launch_bounds__(kTile)
     prescale_kernel(const float4* __restrict__ yl, const EmState* __restrict__ st, const int* __restrict__ tab,
                     const int* __restrict__ done_count, int mode, float* __restrict__ rec, Geo g) {
+  pdl_wait();
+  pdl_launch_dependents();
   if (*done_count >= g.P) return;
   const int tile = blockIdx.x;
   const EmState* sp = st + tab[g.o_tile_pair + tile];
@@ -339,6 +342,8 @@ __global__ void __launch_bounds__(kShiftThreads)
     shift_kernel(const float4* __restrict__ xs, const float* __restrict__ part, const EmState* __restrict__ st,
                  const int* __restrict__ tab, const int* __restrict__ done_count, int cf_x,
                  float* __restrict__ ls_n, float* __restrict__ gam_n, Geo g) {
+  pdl_wait();
+  pdl_launch_dependents();
   if (*done_count >= g.P) return;
   // every CTA covers kShiftThreads sources of one source block (SB is a multiple)
   const long long n = static_cast<long long>(blockIdx.x) * kShiftThreads + threadIdx.x;
@@ -384,6 +389,8 @@ __global__ void __launch_bounds__(kCombineThreads)
                    const float* __restrict__ gam_n, double* __restrict__ rows, float* __restrict__ per_n, Geo g) {
   __shared__ float buf[kCombineWarps][32 * kCPad];
   __shared__ double acc[kCombineWarps][kGlob];
+  pdl_wait();
+  pdl_launch_dependents();
   if (*done_count >= g.P) return;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -529,6 +536,8 @@ constexpr int kReduceWarps = 4;
 __global__ void final_reduce_kernel(const double* __restrict__ rows, const int* __restrict__ tab,
                                     const EmState* __restrict__ st, const int* __restrict__ done_count,
                                     double* __restrict__ mom, Geo g) {
+  pdl_wait();
+  pdl_launch_dependents();
   if (*done_count >= g.P) return;
   const int pair = blockIdx.y;
   if (st[pair].done) return;
@@ -548,9 +557,8 @@ __global__ void final_reduce_kernel(const double* __restrict__ rows, const int* 
 template <int S, int MODE>
 cudaError_t launch_estep_t(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec,
                            const float* ls_n, float* part, int* status, cudaStream_t s) {
-  estep_kernel<S, MODE><<<p.g.grid, warps_for<S>() * 32, p.smem_bytes, s>>>(xs, rec, d.st, ls_n, part, d.tab,
-                                                                           d.done_count, status, p.g);
-  return cudaGetLastError();
+  return launch_k(estep_kernel<S, MODE>, dim3(p.g.grid), dim3(warps_for<S>() * 32), p.smem_bytes, s, xs, rec, d.st,
+                  ls_n, part, d.tab, d.done_count, status, p.g);
 }
 
 int resident_ctas(int S) {
@@ -646,8 +654,7 @@ cudaError_t launch_estep(const BatchPlan& p, const Dev& d, const float4* xs, con
 
 cudaError_t launch_prescale(const BatchPlan& p, const Dev& d, const float4* yl, int mode, float* rec,
                             cudaStream_t s) {
-  prescale_kernel<<<p.g.T, kTile, 0, s>>>(yl, d.st, d.tab, d.done_count, mode, rec, p.g);
-  return cudaGetLastError();
+  return launch_k(prescale_kernel, dim3(p.g.T), dim3(kTile), 0, s, yl, d.st, d.tab, d.done_count, mode, rec, p.g);
 }
 
 cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, const float* rec, int cf_x,
@@ -660,23 +667,20 @@ cudaError_t launch_shift(const BatchPlan& p, const Dev& d, const float4* xs, con
   }
   if (e != cudaSuccess) return e;
   const long long blocks = static_cast<long long>(p.g.B) * p.g.SB / kShiftThreads;
-  shift_kernel<<<static_cast<unsigned>(blocks), kShiftThreads, 0, s>>>(xs, part, d.st, d.tab, d.done_count, cf_x,
-                                                                      ls_n, gam_n, p.g);
-  return cudaGetLastError();
+  return launch_k(shift_kernel, dim3(static_cast<unsigned>(blocks)), dim3(kShiftThreads), 0, s, xs, part, d.st, d.tab,
+                  d.done_count, cf_x, ls_n, gam_n, p.g);
 }
 
 cudaError_t launch_combine(const BatchPlan& p, const Dev& d, const float4* xs, const float* part, int mode,
                            int cf_x, const float* ls_n, const float* gam_n, double* rows, float* per_n,
                            cudaStream_t s) {
-  combine_kernel<<<p.g.combine_ctas, kCombineThreads, 0, s>>>(xs, part, d.tab, d.off64, d.st, d.done_count,
-                                                              mode, cf_x, ls_n, gam_n, rows, per_n, p.g);
-  return cudaGetLastError();
+  return launch_k(combine_kernel, dim3(p.g.combine_ctas), dim3(kCombineThreads), 0, s, xs, part, d.tab, d.off64, d.st,
+                  d.done_count, mode, cf_x, ls_n, gam_n, rows, per_n, p.g);
 }
 
 cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* rows, double* mom, cudaStream_t s) {
   dim3 grid((kGlob + kReduceWarps - 1) / kReduceWarps, static_cast<unsigned>(p.g.P));
-  final_reduce_kernel<<<grid, 32 * kReduceWarps, 0, s>>>(rows, d.tab, d.st, d.done_count, mom, p.g);
-  return cudaGetLastError();
+  return launch_k(final_reduce_kernel, grid, dim3(32 * kReduceWarps), 0, s, rows, d.tab, d.st, d.done_count, mom, p.g);
 }
 
 }  // namespace lsg

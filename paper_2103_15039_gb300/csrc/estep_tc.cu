@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
+  pdl_wait();
   if (*done_count >= g.P) return;
   const int* tile_off = tab + g.o_tile_off;
   const int* block_pair = tab + g.o_block_pair;
@@ -555,9 +556,8 @@ cudaError_t launch_tc_t(const BatchPlan& p, const Dev& d, const float4* xs, cons
   cudaError_t e = cudaFuncSetAttribute(estep_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kTcSmem));
   if (e != cudaSuccess) return e;
-  estep_tc_kernel<MODE><<<p.g.grid, kTcThreads, kTcSmem, s>>>(xs, rec, feat, d.st, ls_n, part, d.tab, d.done_count,
-                                                              status, p.g);
-  return cudaGetLastError();
+  return launch_k(estep_tc_kernel<MODE>, dim3(p.g.grid), dim3(kTcThreads), kTcSmem, s, xs, rec, feat, d.st, ls_n, part,
+                  d.tab, d.done_count, status, p.g);
 }
 }  // namespace
 

@@ -185,6 +185,38 @@ int estep_resident_ctas(int S);
 int estep_warps(int S);
 size_t estep_smem_bytes();  // dynamic shared memory of the FP32 E-step kernel
 
+// ----- programmatic dependent launch (the captured EM loop) ----------------
+// While the EM loop is captured, its kernels are launched with programmatic
+// stream serialisation: a kernel may be scheduled while its predecessor
+// finishes, and waits for the predecessor's completion (hence for everything
+// before it) before its first memory access (pdl_wait).  Kernels launched
+// without the attribute pass pdl_wait at once.
+void set_pdl(bool on);  // launches of this host thread use the attribute while on
+bool pdl_on();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  if (pdl_on()) {
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// let the next kernel of the stream be scheduled (it still waits in pdl_wait for this one)
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
 // Device pointers of a batch.
 struct Dev {
   const int* tab;

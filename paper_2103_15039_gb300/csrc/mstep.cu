@@ -567,6 +567,8 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
                                                               double* __restrict__ trace_all, int trace_iters,
                                                               int* __restrict__ done_count, int P) {
   __shared__ Shared s;
+  pdl_wait();
+  pdl_launch_dependents();
   if (*done_count >= P) return;
   const int pair = blockIdx.x;
   EmState* st = st_all + pair;
@@ -702,8 +704,8 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
 
 cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* mom, const DevParams& dp, double* trace,
                          int trace_iters, cudaStream_t s) {
-  mstep_em_kernel<<<p.g.P, kMThreads, 0, s>>>(mom, d.st, dp, trace, trace_iters, d.done_count, p.g.P);
-  return cudaGetLastError();
+  return launch_k(mstep_em_kernel, dim3(p.g.P), dim3(kMThreads), 0, s, mom, d.st, dp, trace, trace_iters,
+                  d.done_count, p.g.P);
 }
 
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s) {
