@@ -208,7 +208,7 @@ class ClockSampler:
 def kernel_source_hash(precision=0):
     """sha256 over the sources that define the E-step kernel (its file and its copy pipeline)."""
     h = hashlib.sha256()
-    for name in (("estep_tc.cu",) if precision >= 2 else ("estep.cu",)) + ("pipeline.cuh",):
+    for name in (("estep_tc.cu",) if precision >= 2 else ("estep.cu",)) + ("estep_common.cuh", "pipeline.cuh"):
         with open(os.path.join(ROOT, "paper_2103_15039_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

@@ -37,6 +37,7 @@
 // No tensor cores: the contraction depth is 3, so the work is FP32-pipe bound.
 #include <math.h>
 
+#include "estep_common.cuh"
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -51,12 +52,6 @@ template <int S>
 __host__ __device__ constexpr int warps_for() { return S >= 4 ? 8 : 4; }
 template <int S>
 __host__ __device__ constexpr int min_ctas_for() { return S >= 4 ? 1 : 3; }
-
-__device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
-  return y;
-}
 
 // 2^-q for both halves through one packed f16x2 MUFU.EX2 (the mixed-precision
 // variant): -q is rounded to f16 (11-bit significand), the result widened back.
@@ -84,7 +79,6 @@ struct Tgt {  // two consecutive targets, one per half
   float2 ny0, ny1, ny2, lam, a0, a1, a2, q00, q01, q02, q11, q12, q22, b0, b1, b2;
 };
 
-__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // One source against two targets: 21 packed FP32 operations (22 + 1 with
 // per-source shifts) and 2 EX2 (one packed f16x2 EX2 with MODE 2).
@@ -179,16 +173,6 @@ __device__ __forceinline__ void store_acc(float* dst, int SB, int nl, const Acc&
   dst[10 * SB + nl] = a.d.x + a.d.y;
   if (MAXS) dst[11 * SB + nl] = a.el.x + a.el.y;
 }
-
-// Producer/consumer cursor over a CTA's units: (source block, unit) advancing
-// monotonically; the block of a unit is found by walking unit_off forward.
-struct Cursor {
-  int b;
-  __device__ __forceinline__ int advance(const int* unit_off, long long u) {
-    while (u >= unit_off[b + 1]) ++b;
-    return b;
-  }
-};
 
 template <int S, int MODE>
 __global__ void __launch_bounds__(warps_for<S>() * 32, min_ctas_for<S>())

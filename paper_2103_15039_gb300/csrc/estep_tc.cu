@@ -45,6 +45,7 @@
 // with 4 sources per thread (source blocks of 1024), so the combine is shared.
 #include <math.h>
 
+#include "estep_common.cuh"
 #include "internal.cuh"
 #include "pipeline.cuh"
 
@@ -92,28 +93,7 @@ __device__ __forceinline__ uint64_t feat_desc(uint32_t a) {
 
 __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ float ex2_neg(float x) {  // 2^-x
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
-  return y;
-}
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
 
 // Bounded wait that also gives up once another role of the CTA has aborted.  The
 // producer and MMA threads (`idle_role`) pass a suspend-time hint to try_wait, so that
@@ -187,15 +167,6 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&d)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-struct Cursor {  // source block of a unit; units advance monotonically
-  int b;
-  __device__ __forceinline__ int advance(const int* unit_off, long long u) {
-    while (u >= unit_off[b + 1]) ++b;
-    return b;
-  }
-};
-
-__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
 // MODE: 0 uniform shift, 1 per-source shift L_n (El accumulated through the lambda feature).
 template <int MODE>
