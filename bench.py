@@ -142,7 +142,7 @@ def config_obj(c, seed, iters, n_gpus, precision=0, name="rgbd20k"):
             "em_iters": iters, "knn_k": 10, "w": 0.1, "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
             **extra,
             "e_step": E_STEP_DESC[precision],
-            "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
+            "m_step": "double-float Newton (FP32 pairs) on FP64 moments", "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"replicas x{n_gpus} (independent pairs per GPU)"}
 
 
@@ -619,7 +619,7 @@ def run_batch(args):
                       "alpha_max": 2.0, "lambda": 0.2, "seed": seed,
                       "e_step": "fp32 (packed f32x2) + ex2.approx" if args.precision == 0
                       else "fp32 residuals + f16x2 ex2.approx",
-                      "m_step": "fp64", "l2": "flushed between steps (256 MiB write)",
+                      "m_step": "double-float Newton (FP32 pairs) on FP64 moments", "l2": "flushed between steps (256 MiB write)",
                       "parallelism": f"replicas x{ws} (independent batches per GPU)"},
            "em_iters_per_s": ws * iters_run / (ms / 1e3),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xfer["h2d_bytes"],

@@ -22,6 +22,11 @@
  *  - A context serves one call at a time (not thread-safe).
  *  - Rotations are row-major 3x3 doubles, translations 3 doubles, in the
  *    caller's (uncentred) frame: y ~ R x + t.
+ *  - Size limit: the E step's work tables count (source block x target tile)
+ *    units in 32-bit integers; a problem (or a context's capacity) with more
+ *    than 2^30 units in its finest tiling, sum over pairs of
+ *    ceil(N_i / 128) ceil(M_i / 128), is rejected with EINVAL (a single pair
+ *    of N = M = 4,000,000 is within the limit).
  */
 #ifndef LSGCPD_H_
 #define LSGCPD_H_

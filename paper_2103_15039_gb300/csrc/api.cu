@@ -91,6 +91,11 @@ struct lsgcpd_ctx {
 
 namespace {
 
+// Message of the size limit of the plan tables (lsg::plan_fits).
+constexpr const char* kTooLarge =
+    "problem too large: more than 2^30 (source block x target tile) units (a single pair of N = M = 4,000,000 "
+    "is within the limit)";
+
 lsgcpd_status fail(lsgcpd_ctx* c, lsgcpd_status s, const std::string& msg) {
   if (c) c->err = msg;
   return s;
@@ -451,6 +456,7 @@ lsgcpd_status compact_side(lsgcpd_ctx* c, const float* rows, const float* phi, s
 lsgcpd_status stage(lsgcpd_ctx* c, const float* X, const float* Y, const std::vector<long long>& N,
                     const std::vector<long long>& M, const lsgcpd_params* p, bool xd, bool yd, Staged* in) {
   cudaStream_t s = c->stream;
+  if (!plan_fits(N, M)) return fail(c, LSGCPD_EINVAL, kTooLarge);
   long long Ntot = 0, Mtot = 0;
   for (long long v : N) Ntot += v;
   for (long long v : M) Mtot += v;
@@ -816,7 +822,7 @@ void lsgcpd_params_default(lsgcpd_params* p) {
 lsgcpd_status lsgcpd_create(lsgcpd_ctx** out, int device, int64_t max_N, int64_t max_M) {
   if (!out) return LSGCPD_EINVAL;
   *out = nullptr;
-  if (max_N < 1 || max_M < 1) return LSGCPD_EINVAL;
+  if (max_N < 1 || max_M < 1 || !lsg::plan_fits({max_N}, {max_M})) return LSGCPD_EINVAL;
   lsgcpd_ctx* c = new lsgcpd_ctx();
   c->device = device;
   auto bail = [&](lsgcpd_status s) {
@@ -1018,6 +1024,7 @@ lsgcpd_status lsgcpd_preprocess(lsgcpd_ctx* c, const float* Y, int64_t M, const 
   if (ps != LSGCPD_OK) return ps;
   const int k = p->knn_k;
   if (k < 1 || k > kMaxK || k > M) return fail(c, LSGCPD_EINVAL, "knn_k must satisfy 1 <= k <= min(M, 32)");
+  if (!plan_fits({M}, {M})) return fail(c, LSGCPD_EINVAL, kTooLarge);
   LSG_CUDA(enter(c, stream), "stream");
   // a batch of one whose source cloud is Y itself (only the target side is used)
   const BatchPlan plan = plan_batch({M}, {M}, c->num_sms, 1);
@@ -1067,6 +1074,7 @@ lsgcpd_status estep_impl(lsgcpd_ctx* c, const float* X, int64_t N, const float* 
     if (!is_finite_d(R[i])) return fail(c, LSGCPD_EINVAL, "R must be finite");
   for (int i = 0; i < 3; ++i)
     if (!is_finite_d(t[i])) return fail(c, LSGCPD_EINVAL, "t must be finite");
+  if (!plan_fits({N}, {M})) return fail(c, LSGCPD_EINVAL, kTooLarge);
   LSG_CUDA(enter(c, stream), "stream");
   const bool tc = p->precision == 2;
   const BatchPlan plan = plan_batch({N}, {M}, c->num_sms, tc ? 4 : 0);

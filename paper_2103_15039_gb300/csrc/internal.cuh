@@ -173,6 +173,11 @@ struct BatchPlan {
   size_t smem_bytes;
 };
 
+// Upper limit of the plan's 32-bit tables: (source block x target tile) units and tiles.
+constexpr long long kMaxPlanUnits = 1LL << 30;
+// True when every pair has N, M >= 1 and the plan of the batch stays within kMaxPlanUnits
+// for every source tile (a single pair of N = M = 4,000,000 fits; about 4.2 million does not).
+bool plan_fits(const std::vector<long long>& N, const std::vector<long long>& M);
 // Plan a batch (sizes N[i], M[i]); S_override in {1, 2, 4} forces the
 // sources per thread, 0 chooses.  seg_cap: target tiles a CTA sums into one
 // partial slot at most (the length of an FP32 accumulation run).

@@ -5,6 +5,21 @@
 
 namespace lsg {
 
+bool plan_fits(const std::vector<long long>& N, const std::vector<long long>& M) {
+  // the tables index (source block x target tile) units, blocks and tiles with 32-bit ints;
+  // the smallest source block (one source per thread) gives the most units
+  const long long SB = estep_warps(1) * 32LL;
+  long long U = 0, T = 0;
+  for (size_t i = 0; i < N.size(); ++i) {
+    if (N[i] < 1 || M[i] < 1 || N[i] > kMaxPlanUnits * SB || M[i] > kMaxPlanUnits * kTile) return false;
+    const long long tiles = (M[i] + kTile - 1) / kTile;
+    U += ((N[i] + SB - 1) / SB) * tiles;
+    T += tiles;
+    if (U > kMaxPlanUnits || T > kMaxPlanUnits) return false;
+  }
+  return true;
+}
+
 BatchPlan plan_batch(const std::vector<long long>& N, const std::vector<long long>& M, int num_sms,
                      int S_override, int seg_cap) {
   BatchPlan p{};

@@ -20,6 +20,7 @@ int failures = 0;
 
 void check_plan(const std::vector<long long>& N, const std::vector<long long>& M, int sms, int S,
                 int seg_cap = lsg::kSegCap) {
+  EXPECT(lsg::plan_fits(N, M));
   const lsg::BatchPlan plan = lsg::plan_batch(N, M, sms, S, seg_cap);
   EXPECT(plan.g.seg_cap == seg_cap);
   const lsg::Geo& g = plan.g;
@@ -146,6 +147,19 @@ int main() {
   }
   check_plan({500000}, {500000}, 152, 4, 16);
   ++cases;
+  // the size limit of the 32-bit tables: 2^30 units with one source per thread (128-source blocks)
+  EXPECT(lsg::plan_fits({4000000}, {4000000}));
+  EXPECT(lsg::plan_fits({4194304}, {4194304}));  // 32768 blocks x 32768 tiles = 2^30 units
+  EXPECT(!lsg::plan_fits({4194305}, {4194304}));
+  EXPECT(!lsg::plan_fits({4194304}, {4194305}));
+  EXPECT(!lsg::plan_fits({4000000, 4000000}, {4000000, 4000000}));
+  EXPECT(!lsg::plan_fits({0}, {10}));
+  EXPECT(!lsg::plan_fits({10}, {0}));
+  {
+    const lsg::BatchPlan big = lsg::plan_batch({4194304}, {4194304}, 152, 1);
+    EXPECT(big.g.U == lsg::kMaxPlanUnits);
+    EXPECT(big.g.total_slots > 0 && big.g.grid == 152);
+  }
   std::printf("%d plans checked, %d failures\n", cases, failures);
   return failures != 0;
 }

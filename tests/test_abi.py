@@ -76,4 +76,7 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     h = ctypes.c_void_p()
     assert L.lsgcpd_create(ctypes.byref(h), 0, 0, 5) == 1
     assert L.lsgcpd_create(ctypes.byref(h), 0, 5, -1) == 1
+    # capacity beyond the 2^30-unit limit of the plan tables (4.2e6 x 4.2e6 in 128 x 128 tiles)
+    assert L.lsgcpd_create(ctypes.byref(h), 0, 4_200_000, 4_200_000) == 1
+    assert not h.value
     assert L.lsgcpd_last_error(None) == b"null context"

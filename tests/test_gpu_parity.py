@@ -159,6 +159,15 @@ def test_invalid_arguments_report_einval(ctx):
     with pytest.raises(binding.LsgcpdError):
         ctx.register(np.random.rand(5, 3).astype(np.float32), np.random.rand(50, 3).astype(np.float32),
                      binding.default_params(w=1.0))
+    # beyond the 2^30-unit limit of the plan tables (4.2e6 targets in 128 x 128 tiles): rejected
+    # before any work, and the context stays usable
+    big = torch.zeros((4_200_000, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(binding.LsgcpdError) as e:
+        ctx.preprocess(big, binding.default_params())
+    assert e.value.status == 1 and "too large" in str(e.value)
+    del big
+    Y = synth.sphere_plane_pair(seed=3, n=10, m=200)["Y"]
+    assert ctx.preprocess(_cuda(Y), binding.default_params())["normals"].shape[0] == 200
     torch.cuda.synchronize()
 
 
