@@ -27,7 +27,9 @@
 // M1, the gradient, the objective change dQ = 2 <M1, D> + <D, G D> of a trial
 // step D, the transform and Q_d are double-float values (pairs of FP32 numbers,
 // about 48 significant bits) computed lane-parallel on the FP32 pipe; the model
-// arrives in FP64 and is converted once.  The Hessian and the 6x6 solve for the
+// arrives in FP64 and is split once, with integer bit operations (an FP64
+// instruction has ~80 cycles of latency on GB300, a conversion chain several times
+// that).  The Hessian and the 6x6 solve for the
 // Newton direction (LDL^T) are FP32: an inexact direction only changes the path,
 // not the fixed point, which is set by the double-float residual (iterative
 // refinement).
@@ -40,13 +42,103 @@ namespace {
 
 constexpr int kMThreads = 128;
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic for the Newton loop: a value is hi + lo (|lo| at most
+// half an ulp of hi), about 48 significant bits, computed on the FP32 pipe with
+// the error-free transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the
+// FMA-based exact product.  GB300 issues FP64 instructions far more slowly than
+// FP32 ones and the loop is a chain of dependent operations, so its state, the
+// model it needs for the objective change, and every operation on them use
+// these pairs; the Hessian only steers the direction and is FP32.
+// ---------------------------------------------------------------------------
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd dd_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - static_cast<double>(h))};
+}
+__device__ __forceinline__ double dd_to(dd a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+// The same split with integer operations only (FP64 instructions have a latency of ~80
+// cycles on GB300, and a conversion chain several times that): hi = x truncated to 24
+// significant bits (exact bit surgery), lo = the remaining 29 bits rounded to FP32, so
+// hi + lo carries about 48 bits of x.  Magnitudes below 2^-126 flush to zero, above the
+// FP32 range hi is an infinity; infinities and NaN pass through in hi.
+__device__ __forceinline__ dd dd_split(double x) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  const unsigned sign = static_cast<unsigned>(u >> 32) & 0x80000000u;
+  const int e = static_cast<int>((u >> 52) & 0x7ffu);
+  const unsigned long long m = u & 0xfffffffffffffULL;
+  if (e == 0x7ff) return {__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f};
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return {__uint_as_float(sign), 0.f};
+  if (ef >= 255) return {__uint_as_float(sign | 0x7f800000u), 0.f};
+  const float hi = __uint_as_float(sign | (static_cast<unsigned>(ef) << 23) | static_cast<unsigned>(m >> 29));
+  const float lo = ldexpf(static_cast<float>(static_cast<unsigned>(m & 0x1fffffffu)), e - 1075);
+  return {hi, sign ? -lo : lo};
+}
+__device__ __forceinline__ float dd_f(dd a) { return __fadd_rn(a.hi, a.lo); }
+
+__device__ __forceinline__ dd two_sum(float a, float b) {  // s + e = a + b exactly
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd two_prod(float a, float b) {  // p + e = a b exactly
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  const dd t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_mulf(dd a, float b) {  // b exact in FP32
+  dd p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+__device__ __forceinline__ dd dd_scale2(dd a, float s) { return {a.hi * s, a.lo * s}; }  // s a power of two
+__device__ __forceinline__ bool dd_le0(dd a) { return a.hi < 0.f || (a.hi == 0.f && a.lo <= 0.f); }
+
 // Power-series coefficients (-1)^k / (2k + o)! of sin(th)/th (o = 1), (1 - cos th)/th^2
 // (o = 2) and (th - sin th)/th^3 (o = 3) in powers of th^2, k = 0..8; the truncation
 // error is below 1e-19 for th^2 <= 1/4.
-__device__ const double c_exp_series[3][9] = {
+constexpr double kExpSeries[3][9] = {
     {1.0, -0.16666666666666666, 0.008333333333333333, -0.0001984126984126984, 2.7557319223985893e-06, -2.505210838544172e-08, 1.6059043836821613e-10, -7.647163731819816e-13, 2.8114572543455206e-15},
     {0.5, -0.041666666666666664, 0.001388888888888889, -2.48015873015873e-05, 2.755731922398589e-07, -2.08767569878681e-09, 1.1470745597729725e-11, -4.779477332387385e-14, 1.5619206968586225e-16},
     {0.16666666666666666, -0.008333333333333333, 0.0001984126984126984, -2.7557319223985893e-06, 2.505210838544172e-08, -1.6059043836821613e-10, 7.647163731819816e-13, -2.8114572543455206e-15, 8.22063524662433e-18}};
+
+// The same coefficients as double-float pairs (hi = the FP32 rounding, lo = the FP32
+// rounding of the rest), split at compile time.
+struct SeriesTab {
+  dd c[3][9];
+};
+__host__ __device__ constexpr SeriesTab make_series_tab() {
+  SeriesTab t{};
+  for (int o = 0; o < 3; ++o)
+    for (int k = 0; k < 9; ++k) {
+      const float hi = static_cast<float>(kExpSeries[o][k]);
+      t.c[o][k] = dd{hi, static_cast<float>(kExpSeries[o][k] - static_cast<double>(hi))};
+    }
+  return t;
+}
+__device__ const SeriesTab c_series = make_series_tab();
 
 // Gradient and symmetrised Hessian entries as fixed linear combinations of the
 // entries of C (10 pairs x 9) and of NM = R^T M1 (3 x 4):
@@ -137,62 +229,6 @@ __host__ __device__ constexpr HessTab make_hess_tab() {
 
 __device__ const HessTab c_hess = make_hess_tab();
 
-// ---------------------------------------------------------------------------
-// Double-float arithmetic for the Newton loop: a value is hi + lo (|lo| at most
-// half an ulp of hi), about 48 significant bits, computed on the FP32 pipe with
-// the error-free transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the
-// FMA-based exact product.  GB300 issues FP64 instructions far more slowly than
-// FP32 ones and the loop is a chain of dependent operations, so its state, the
-// model it needs for the objective change, and every operation on them use
-// these pairs; the Hessian only steers the direction and is FP32.
-// ---------------------------------------------------------------------------
-struct dd {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dd dd_from(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - static_cast<double>(h))};
-}
-__device__ __forceinline__ double dd_to(dd a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
-__device__ __forceinline__ float dd_f(dd a) { return __fadd_rn(a.hi, a.lo); }
-
-__device__ __forceinline__ dd two_sum(float a, float b) {  // s + e = a + b exactly
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ dd fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dd two_prod(float a, float b) {  // p + e = a b exactly
-  const float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
-}
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.hi, b.hi);
-  const dd t = two_sum(a.lo, b.lo);
-  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
-}
-__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  dd p = two_prod(a.hi, b.hi);
-  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
-  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
-  return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ dd dd_mulf(dd a, float b) {  // b exact in FP32
-  dd p = two_prod(a.hi, b);
-  p.lo = __fmaf_rn(a.lo, b, p.lo);
-  return fast_two_sum(p.hi, p.lo);
-}
-__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
-__device__ __forceinline__ dd dd_scale2(dd a, float s) { return {a.hi * s, a.lo * s}; }  // s a power of two
-__device__ __forceinline__ bool dd_le0(dd a) { return a.hi < 0.f || (a.hi == 0.f && a.lo <= 0.f); }
-
 // theta^2 = w . w for a rotation part given exactly in FP32
 __device__ __forceinline__ dd theta2(const float* w) {
   return dd_add(dd_add(two_prod(w[0], w[0]), two_prod(w[1], w[1])), two_prod(w[2], w[2]));
@@ -200,9 +236,7 @@ __device__ __forceinline__ dd theta2(const float* w) {
 
 struct Shared {
   double SD, NP;
-  double H1[12];
-  double R[9], t[3];    // the pose in FP64 (start and result of the Newton loop)
-  double Ro[9], to[3];  // the E step's pose T_o
+  double R[9], t[3];  // the result of the Newton loop in FP64
   double Q;
   float gHf[27];  // gradient (6) then the upper triangle of H_s (21), FP32 for the direction solve
   float xf[6];    // Newton direction (FP32)
@@ -218,8 +252,9 @@ struct Shared {
   // double-float state of the loop (hi, lo pairs)
   dd Ad[10][6];  // the model for G D
   dd Rd[9], td[3], M1d[12], NMd[12], Qd, dQd;
+  dd Rod[9], tod[3];  // the E step's pose T_o
   dd coefd[3], Ed[9], Vvd[3], Tcd[12], dld[12], Gdd[12], dqv[12];
-  dd seriesd[3][9];
+  SeriesTab series;
 };
 
 // position of (a, b), a <= b, in the row-major upper triangle of a 6x6 matrix
@@ -250,30 +285,52 @@ __device__ __forceinline__ double eps3(int a, int b, int c) {
   return ((b - a + 3) % 3 == 1) ? 1.0 : -1.0;
 }
 
-__device__ void load_model(Shared& s, const double* mom) {
+// Constant tables of the Newton loop (Hessian index table, exp-map series) into
+// shared memory.  They do not depend on the E step, so the kernels load them before
+// waiting for their predecessor.
+__device__ void load_tables(Shared& s) {
   const int tid = threadIdx.x;
-  {
-    const int* src = reinterpret_cast<const int*>(&c_hess);
-    int* dst = reinterpret_cast<int*>(&s.hess);
-    // global (not constant) memory: every lane reads a different word, so the loads coalesce
-    constexpr int kWords = static_cast<int>(sizeof(HessTab) / sizeof(int));
+  // global (not constant) memory: every lane reads a different word, so the loads coalesce
+  const int* src = reinterpret_cast<const int*>(&c_hess);
+  int* dst = reinterpret_cast<int*>(&s.hess);
+  constexpr int kWords = static_cast<int>(sizeof(HessTab) / sizeof(int));
 #pragma unroll
-    for (int r = 0; r < (kWords + kMThreads - 1) / kMThreads; ++r) {  // all loads in flight at once
-      const int i = tid + r * kMThreads;
-      if (i < kWords) dst[i] = __ldg(src + i);
-    }
-    if (tid < 27) s.seriesd[tid / 9][tid % 9] = dd_from(__ldg(&c_exp_series[tid / 9][tid % 9]));
+  for (int r = 0; r < (kWords + kMThreads - 1) / kMThreads; ++r) {  // all loads in flight at once
+    const int i = tid + r * kMThreads;
+    if (i < kWords) dst[i] = __ldg(src + i);
   }
-  if (tid == 0) {
-    s.NP = mom[0];
-    s.SD = mom[1];
-  }
-  if (tid < 12) s.H1[tid] = mom[2 + tid];
+  constexpr int kSeriesWords = static_cast<int>(sizeof(SeriesTab) / sizeof(int));
+  static_assert(kSeriesWords <= kMThreads, "one word per thread");
+  if (tid < kSeriesWords)
+    reinterpret_cast<int*>(&s.series)[tid] = __ldg(reinterpret_cast<const int*>(&c_series) + tid);
+}
+
+// Model, start pose and loop state of the Newton loop from the global moments (FP64)
+// and the pose T_o = (R, t) (FP64), all lanes in parallel and without FP64
+// instructions; the caller synchronises before newton().
+__device__ void setup_newton(Shared& s, const double* mom, const double* R, const double* t) {
+  const int tid = threadIdx.x;
   if (tid < 60) {
     const int p = tid / 10, q = tid % 10;  // moments are ordered A pair major, xt pair minor
-    const double a = mom[14 + tid];
-    s.Ad[q][p] = dd_from(a);
-    s.Af[q][p] = static_cast<float>(a);
+    const dd a = dd_split(mom[14 + tid]);
+    s.Ad[q][p] = a;
+    s.Af[q][p] = dd_f(a);
+  } else if (tid >= 64 && tid < 76) {
+    s.M1d[tid - 64] = dd_split(mom[2 + tid - 64]);  // M1 = H1 at T = T_o
+  } else if (tid >= 76 && tid < 85) {
+    const dd r = dd_split(R[tid - 76]);
+    s.Rd[tid - 76] = r;
+    s.Rod[tid - 76] = r;
+  } else if (tid >= 85 && tid < 88) {
+    const dd v = dd_split(t[tid - 85]);
+    s.td[tid - 85] = v;
+    s.tod[tid - 85] = v;
+  } else if (tid == 96) {
+    s.NP = mom[0];
+    s.SD = mom[1];
+    s.Qd = dd_split(mom[1]);
+    s.iters = s.damped = s.halvings = 0;
+    s.go = 1;
   }
 }
 
@@ -324,31 +381,10 @@ __device__ __forceinline__ bool ldl_solve6(const float (&H)[36], const float (&b
   return ok;
 }
 
-// Newton loop on the model in shared memory; T starts at (s.R, s.t) == (s.Ro, s.to).
-// Ends with s.R, s.t and s.Q (FP64) set from the double-float state.
+// Newton loop on the model in shared memory (set up by setup_newton, synchronised);
+// T starts at T_o.  Ends with s.R, s.t and s.Q (FP64) set from the double-float state.
 __device__ void newton(Shared& s, int newton_max, double newton_tol) {
   const int tid = threadIdx.x;
-  // lane tid < 12 owns (G D)_ik, i = tid / 4, k = tid % 4: its 12 model entries
-  // A^{q(k,l)}_{i j} (j = 0..2, l = 0..3) are fixed, so their flat offsets are too
-  int gidx[12];
-  {
-    const int i = (tid / 4) % 3, k = tid % 4;
-#pragma unroll
-    for (int l = 0; l < 4; ++l)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) gidx[3 * l + j] = pair_q(k, l) * 6 + sym_p(i, j);
-  }
-  if (tid < 12) s.M1d[tid] = dd_from(s.H1[tid]);
-  if (tid < 9) {
-    s.Rd[tid] = dd_from(s.R[tid]);
-  } else if (tid < 12) {
-    s.td[tid - 9] = dd_from(s.t[tid - 9]);
-  } else if (tid == 32) {
-    s.Qd = dd_from(s.SD);
-    s.iters = s.damped = s.halvings = 0;
-    s.go = 1;
-  }
-  __syncthreads();
   for (int it = 0; it < newton_max; ++it) {
     // --- C^{kl} = R^T A^{kl} R (FP32: Hessian only) and N, m = R^T M1 (double-float) ---
     if (tid < 60) {
@@ -443,7 +479,7 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
         const dd x = theta2(s.wv);
         dd cf;
         if (x.hi <= 0.25f) {
-          const dd* c = s.seriesd[tid];
+          const dd* c = s.series.c[tid];
           const int top = x.hi < 1e-6f ? 3 : (x.hi < 1e-3f ? 5 : 8);
           dd r = c[top];
           for (int k = top - 1; k >= 0; --k) r = dd_fma(r, x, c[k]);
@@ -500,6 +536,17 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
       if (tid < 32) {  // G D and dQ = 2 <M1, D> + <D, G D>
         if (tid < 12) {
           const dd* Af = &s.Ad[0][0];
+          // lane tid owns (G D)_ik, i = tid / 4, k = tid % 4, from the model entries
+          // A^{q(k,l)}_{i j} (j = 0..2, l = 0..3) (offsets from integer arithmetic: an
+          // array kept across the loop spills)
+          int gidx[12];
+          {
+            const int i = tid / 4, k = tid % 4;
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) gidx[3 * l + j] = pair_q(k, l) * 6 + sym_p(i, j);
+          }
           dd gl[4];
 #pragma unroll
           for (int l = 0; l < 4; ++l) {  // four independent chains of three
@@ -562,27 +609,38 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
 }
 
 // One CTA per pair: its Newton M step, sigma^2 update, trace and E-step constants.
+// Global memory is touched in three rounds: the constant tables (before the wait for
+// the predecessor), then the moments, the counter and a copy of the pair's state (one
+// coalesced read), and at the end the updated state (one coalesced write); every
+// scalar of the epilogue is worked on in shared memory.
+constexpr int kStateWords = static_cast<int>(sizeof(EmState) / sizeof(int));
+static_assert(sizeof(EmState) % sizeof(int) == 0 && kStateWords <= kMThreads, "one word of the state per thread");
+
 __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ mom_all,
                                                               EmState* __restrict__ st_all, DevParams dp,
                                                               double* __restrict__ trace_all, int trace_iters,
                                                               int* __restrict__ done_count, int P) {
   __shared__ Shared s;
+  __shared__ EmState es;
+  __shared__ double nll_sh, pout_sh;
+  __shared__ float dmot[12];
+  __shared__ int finish_sh, nll_stop_sh;  // written by different lanes in the same phase
+  const int tid = threadIdx.x;
+  load_tables(s);
   pdl_wait();
   pdl_launch_dependents();
-  if (*done_count >= P) return;
   const int pair = blockIdx.x;
   EmState* st = st_all + pair;
   const double* mom = mom_all + static_cast<size_t>(pair) * kGlob;
-  double* trace = trace_all ? trace_all + static_cast<size_t>(pair) * trace_iters * 8 : nullptr;
-  if (st->done) return;
-  const int tid = threadIdx.x;
-  load_model(s, mom);
-  if (tid < 9) {
-    s.R[tid] = s.Ro[tid] = st->R[tid];
-  } else if (tid < 12) {
-    s.t[tid - 9] = s.to[tid - 9] = st->t[tid - 9];
+  const int finished = *done_count;
+  if (tid < kStateWords) reinterpret_cast<int*>(&es)[tid] = reinterpret_cast<const int*>(st)[tid];
+  setup_newton(s, mom, st->R, st->t);
+  if (tid == 97) {
+    nll_sh = mom[75];
+    pout_sh = mom[74];
   }
   __syncthreads();
+  if (finished >= P || es.done) return;  // uniform over the CTA
   if (!(s.NP > 0.0)) {
     if (tid == 0) {
       st->numeric_fail = 1;
@@ -592,75 +650,70 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     return;
   }
   newton(s, dp.newton_max, dp.newton_tol);
-  // --- epilogue, lane-parallel: state, E-step constants, diagnostics ---
-  __shared__ float dmot[12];
-  __shared__ double s2_sh;
-  __shared__ int done_sh;
-  if (tid < 9) {
-    dmot[tid] = static_cast<float>(s.R[tid] - s.Ro[tid]);
-  } else if (tid < 12) {
+  // --- epilogue, lane-parallel on the shared copy of the state ---
+  const int it = es.iter;
+  if (tid < 9) {  // rotation change (FP32 suffices for the motion test)
+    dmot[tid] = dd_f(dd_sub(s.Rd[tid], s.Rod[tid]));
+  } else if (tid < 12) {  // translation change of the source centroid: dt - dR mu_x
     const int i = tid - 9;
-    double d = s.t[i] - s.to[i];
-    for (int j = 0; j < 3; ++j) d -= (s.R[3 * i + j] - s.Ro[3 * i + j]) * st->mu_x[j];
-    dmot[tid] = static_cast<float>(d);
-  } else if (tid == 32) {
+    float d = dd_f(dd_sub(s.td[i], s.tod[i]));
+    for (int j = 0; j < 3; ++j)
+      d -= dd_f(dd_sub(s.Rd[3 * i + j], s.Rod[3 * i + j])) * static_cast<float>(es.mu_x[j]);
+    dmot[tid] = d;
+  } else if (tid == 32) {  // sigma^2 and the E-step constants it sets
     const double s2 = s.Q * __drcp_rn(3.0 * s.NP);
-    const bool at_floor = !(s2 > st->sigma2_floor);
-    s2_sh = at_floor ? st->sigma2_floor : s2;
-    const int it = st->iter;
-    done_sh = at_floor || it + 1 >= dp.max_iters;
+    const bool at_floor = !(s2 > es.sigma2_floor);
+    const double s2c = at_floor ? es.sigma2_floor : s2;
+    es.sigma2 = s2c;
+    set_sigma_constants(&es, static_cast<float>(s2c));
+    finish_sh = (at_floor || it + 1 >= dp.max_iters) ? 1 : 0;
+  } else if (tid >= 64 && tid < 76) {  // new pose (FP64) and its FP32 copies for the next E step
+    const int e = tid - 64;
+    if (e < 9) {
+      es.R[e] = s.R[e];
+      es.Rf[e] = static_cast<float>(s.R[e]);
+    } else {
+      es.t[e - 9] = s.t[e - 9];
+      es.tf[e - 9] = static_cast<float>(s.t[e - 9]);
+    }
+  } else if (tid == 96) {  // termination on the log-likelihood of Eq. (4): change since the previous E step
+    const double nll = nll_sh;
+    nll_stop_sh = dp.nll_tol > 0.0 && it > 0 && fabs(nll - es.nll_prev) <= dp.nll_tol * fabs(nll);
+    es.nll_prev = nll;
   }
   __syncthreads();
-  // new pose (FP64) and its FP32 copies for the next E step
-  if (tid < 9) {
-    st->R[tid] = s.R[tid];
-    st->Rf[tid] = static_cast<float>(s.R[tid]);
-  } else if (tid < 12) {
-    st->t[tid - 9] = s.t[tid - 9];
-    st->tf[tid - 9] = static_cast<float>(s.t[tid - 9]);
+  if (tid == 0) {
+    float fro = 0.f;
+    for (int i = 0; i < 9; ++i) fro += dmot[i] * dmot[i];
+    const float ang = 2.f * asinf(fminf(1.f, sqrtf(fro) * 0.35355339f));
+    const float dtr = sqrtf(dmot[9] * dmot[9] + dmot[10] * dmot[10] + dmot[11] * dmot[11]);
+    const float motion = fmaxf(ang, dtr / static_cast<float>(es.diag > 0 ? es.diag : 1.0));
+    if (trace_all) {
+      double* tr = trace_all + (static_cast<size_t>(pair) * trace_iters + it) * 8;
+      tr[0] = es.sigma2;
+      tr[1] = s.NP;
+      tr[2] = s.Q;
+      tr[3] = s.iters;
+      tr[4] = s.damped;
+      tr[5] = motion;
+      tr[6] = nll_sh;
+      tr[7] = pout_sh;
+    }
+    es.iter = it + 1;
+    if (finish_sh || nll_stop_sh || (dp.tol > 0.0 && motion < dp.tol)) {
+      es.done = 1;
+      atomicAdd(done_count, 1);
+    }
   }
-  if (tid != 0) return;
-  float fro = 0.f;
-  for (int i = 0; i < 9; ++i) fro += dmot[i] * dmot[i];
-  const float ang = 2.f * asinf(fminf(1.f, sqrtf(fro) * 0.35355339f));
-  const float dtr = sqrtf(dmot[9] * dmot[9] + dmot[10] * dmot[10] + dmot[11] * dmot[11]);
-  const float motion = fmaxf(ang, dtr / static_cast<float>(st->diag > 0 ? st->diag : 1.0));
-  const double s2 = s2_sh;
-  st->sigma2 = s2;
-  const int it = st->iter;
-  if (trace) {
-    double* tr = trace + static_cast<size_t>(it) * 8;
-    tr[0] = s2;
-    tr[1] = s.NP;
-    tr[2] = s.Q;
-    tr[3] = s.iters;
-    tr[4] = s.damped;
-    tr[5] = motion;
-    tr[6] = mom[75];
-    tr[7] = mom[74];
-  }
-  st->iter = it + 1;
-  // termination on the log-likelihood of Eq. (4): relative change since the previous E step
-  const double nll = mom[75];
-  const bool nll_stop = dp.nll_tol > 0.0 && it > 0 && fabs(nll - st->nll_prev) <= dp.nll_tol * fabs(nll);
-  st->nll_prev = nll;
-  if (done_sh || nll_stop || (dp.tol > 0.0 && motion < dp.tol)) {
-    st->done = 1;
-    atomicAdd(done_count, 1);
-  }
-  // E-step constants (the rotation/translation copies were written above)
-  set_sigma_constants(st, static_cast<float>(s2));
+  __syncthreads();
+  if (tid < kStateWords) reinterpret_cast<int*>(st)[tid] = reinterpret_cast<const int*>(&es)[tid];
 }
 
 __global__ void __launch_bounds__(kMThreads) mstep_standalone_kernel(double* __restrict__ io, DevParams dp) {
   __shared__ Shared s;
   const int tid = threadIdx.x;
-  load_model(s, io);
-  if (tid < 9) {
-    s.R[tid] = s.Ro[tid] = io[80 + tid];
-  } else if (tid < 12) {
-    s.t[tid - 9] = s.to[tid - 9] = io[80 + tid];
-  }
+  load_tables(s);
+  setup_newton(s, io, io + 80, io + 89);
   __syncthreads();
   newton(s, dp.newton_max, dp.newton_tol);
   if (tid != 0) return;
