@@ -134,6 +134,8 @@ E_STEP_DESC = {0: "fp32 (packed f32x2) + ex2.approx",
                2: "fp32 residuals + ex2.approx, exponentials truncated to tf32, moment sums on tcgen05 "
                   "(tf32 x hi/lo features, f32 accumulation in tensor memory)"}
 DTYPE = {0: "f32", 1: "f32+f16", 2: "f32+tf32"}
+# workloads whose line also times the f16x2-exponential path and its error against FP32
+HALF2_WORKLOADS = ("lidar100k", "superquadric500k")
 
 
 def config_obj(c, seed, iters, n_gpus, precision=0, name="rgbd20k"):
@@ -289,17 +291,18 @@ def cpu_baseline(c, got, iters, budget_s=40.0):
     return out, None
 
 
-def oracle_rot(Ra, Rb):
-    import oracle
-    return oracle.rotation_error(Ra, Rb)
+def rotation_angle(Ra, Rb):
+    """Angle of the relative rotation Ra^T Rb, 2 asin(|Ra - Rb|_F / (2 sqrt 2)) (accurate for small angles)."""
+    import numpy as np
+    d = np.linalg.norm(np.asarray(Ra, dtype=np.float64) - np.asarray(Rb, dtype=np.float64))
+    return float(2.0 * np.arcsin(min(1.0, d / (2.0 * np.sqrt(2.0)))))
 
 
 def errors_vs(got, ref, diag):
     """Rotation / translation / sigma^2 error of a GPU result against a reference result."""
     import numpy as np
 
-    import oracle
-    return {"rot_err_rad": oracle.rotation_error(got["R"], ref["R"]),
+    return {"rot_err_rad": rotation_angle(got["R"], ref["R"]),
             "trans_err_rel_diag": float(np.linalg.norm(got["t"] - ref["t"]) / diag),
             "sigma2_rel": abs(got["sigma2"] - ref["sigma2"]) / ref["sigma2"]}
 
@@ -485,6 +488,21 @@ def run_ours(args):
                  "iters_run": got2["iters"],
                  "vs_fp32_result": errors_vs(got2, got, diag)}
         out["mixed_precision"] = mixed
+    # the range-scan workloads also compare the f16x2-exponential path (precision 1) with FP32
+    half = None
+    if args.precision == 0 and not args.no_variants and args.workload in HALF2_WORKLOADS:
+        p1 = binding.default_params(max_iters=iters, precision=1)
+        for _ in range(max(args.warmup, 1)):
+            ctx.register(Xd, Yd, p1)
+        barrier()
+        got1, ms1, est1 = time_registrations(ctx, Xd, Yd, p1, args.steps, flush, stream)
+        barrier()
+        diag = float(np.linalg.norm(c["Y"].max(0).astype(np.float64) - c["Y"].min(0).astype(np.float64)))
+        half = {"precision": 1, "e_step": E_STEP_DESC[1], "dtype": DTYPE[1],
+                "value": job_throughput(got1["iters"] * N * M, ws, ms1), "unit": UNIT, "ms_per_step": round(ms1, 4),
+                "estep_ms_per_launch": round(est1, 5), "speedup_vs_fp32_step": round(ms / ms1, 4),
+                "iters_run": got1["iters"], "vs_fp32_result": errors_vs(got1, got, diag)}
+        out["half2"] = half
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb, ref = cpu_baseline(c, got, iters_run)
         out["cpu_baseline"] = cb
@@ -492,6 +510,17 @@ def run_ours(args):
             out["vs_fp64_oracle"] = errors_vs(got, ref, ref["diag"])
             if mixed:
                 mixed["vs_fp64_oracle"] = errors_vs(got2, ref, ref["diag"])
+        elif half and args.workload == "lidar100k":
+            # the full FP64 registration does not fit the budget: both precisions against the
+            # oracle over the first two EM iterations (about half a minute on 16 cores)
+            import oracle
+            ref2 = oracle.register(c["X"], c["Y"], max_iters=2)
+            diag = float(np.linalg.norm(c["Y"].max(0).astype(np.float64) - c["Y"].min(0).astype(np.float64)))
+            short = {}
+            for prec, key in ((0, "fp32"), (1, "half2")):
+                g2 = ctx.register(Xd, Yd, binding.default_params(max_iters=2, precision=prec))
+                short[key] = errors_vs(g2, ref2, diag)
+            out["vs_fp64_oracle_2_iterations"] = short
     ctx.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -655,7 +684,7 @@ def run_batch(args):
         barrier()
         ms2 = statistics.mean(t2)
         it2 = int(got2["iters"].max())
-        rot = [oracle_rot(got2["R"][i], got["R"][i]) for i in range(P)]
+        rot = [rotation_angle(got2["R"][i], got["R"][i]) for i in range(P)]
         out["mixed_precision"] = {
             "precision": 2, "e_step": E_STEP_DESC[2], "dtype": DTYPE[2],
             "value": job_throughput(float((got2["iters"].astype(np.float64) * nm).sum()), ws, ms2), "unit": UNIT,
