@@ -711,10 +711,6 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     key.timing = c->timing;
     key.trace = trace ? 1 : 0;
     if (!(c->gexec && key == c->gkey)) {
-      if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
       cudaGraph_t gr = nullptr;
       LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
       set_pdl(true);  // consecutive kernels of the loop overlap their launch with the predecessor's tail
@@ -743,7 +739,21 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         if (gr) cudaGraphDestroy(gr);
         return cuda_fail(c, ce != cudaSuccess ? ce : ee, "graph capture");
       }
-      cudaError_t ie = cudaGraphInstantiate(&c->gexec, gr, 0);
+      // the same loop for another problem (same node sequence, other sizes and launch
+      // shapes): update the executable graph's parameters in place, a fraction of the cost
+      // of instantiating it; anything the update cannot express is instantiated afresh
+      bool updated = false;
+      if (c->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->gexec, gr, &info) == cudaSuccess) {
+          updated = true;
+        } else {
+          cudaGetLastError();
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+      }
+      cudaError_t ie = updated ? cudaSuccess : cudaGraphInstantiate(&c->gexec, gr, 0);
       cudaGraphDestroy(gr);
       if (ie != cudaSuccess) {
         c->gexec = nullptr;

@@ -92,6 +92,29 @@ def test_register_batch_shapes(ctx):
         _check(got, ref, pr["Y"])
 
 
+def test_alternating_shapes_reuse_the_loop_graph_with_identical_results():
+    """Consecutive registrations of other shapes update the captured EM loop in place (or
+    rebuild it when the kernel sequence changes, e.g. the per-source shift mode of w = 0):
+    every result equals, bit for bit, the same registration in a fresh context."""
+    shapes = [(800, 900, 0.1), (1000, 1000, 0.1), (1200, 700, 0.1), (900, 1100, 0.0), (800, 900, 0.1)]
+    pairs = [synth.sphere_plane_pair(seed=40 + i, n=n, m=m) for i, (n, m, _) in enumerate(shapes)]
+    fresh = []
+    for (n, m, w), c in zip(shapes, pairs):
+        ctx1 = binding.Context(0, 2000, 2000)
+        ctx1.set_autotune(False)
+        fresh.append(ctx1.register(c["X"], c["Y"], binding.default_params(w=w)))
+        ctx1.close()
+    shared = binding.Context(0, 2000, 2000)
+    shared.set_autotune(False)
+    for rep in range(2):
+        for (n, m, w), c, ref in zip(shapes, pairs, fresh):
+            got = shared.register(c["X"], c["Y"], binding.default_params(w=w))
+            np.testing.assert_array_equal(got["R"], ref["R"])
+            np.testing.assert_array_equal(got["t"], ref["t"])
+            assert got["sigma2"] == ref["sigma2"] and got["iters"] == ref["iters"]
+    shared.close()
+
+
 def test_register_rgbd_full_size(ctx):
     """The benchmark's workload (20,000 x 20,000, RGBD room), first 8 iterations."""
     c = synth.rgbd_room_pair()
