@@ -551,6 +551,9 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
     return;
   }
   const long long gm = m0 + m;
+  // FP64 throughput is the bound of this kernel on GB300 (a division costs about a dozen
+  // FP64 instructions): the six distinct sums of the covariance are scaled once by 1/k
+  const double inv_k = 1.0 / k;
   double mean[3] = {0.0, 0.0, 0.0};
   for (int j = 0; j < k; ++j) {
     const long long q = m0 + idx[gm * k + j];
@@ -558,14 +561,21 @@ __global__ void __launch_bounds__(kTile) geometry_kernel(const float* __restrict
     mean[1] += Y[3 * q + 1];
     mean[2] += Y[3 * q + 2];
   }
-  for (int c = 0; c < 3; ++c) mean[c] /= k;
-  double C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int c = 0; c < 3; ++c) mean[c] *= inv_k;
+  double s00 = 0.0, s01 = 0.0, s02 = 0.0, s11 = 0.0, s12 = 0.0, s22 = 0.0;
   for (int j = 0; j < k; ++j) {
     const long long q = m0 + idx[gm * k + j];
-    const double d[3] = {Y[3 * q] - mean[0], Y[3 * q + 1] - mean[1], Y[3 * q + 2] - mean[2]};
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) C[r][c] += d[r] * d[c] / k;
+    const double d0 = Y[3 * q] - mean[0], d1 = Y[3 * q + 1] - mean[1], d2 = Y[3 * q + 2] - mean[2];
+    s00 = fma(d0, d0, s00);
+    s01 = fma(d0, d1, s01);
+    s02 = fma(d0, d2, s02);
+    s11 = fma(d1, d1, s11);
+    s12 = fma(d1, d2, s12);
+    s22 = fma(d2, d2, s22);
   }
+  double C[3][3] = {{s00 * inv_k, s01 * inv_k, s02 * inv_k},
+                    {s01 * inv_k, s11 * inv_k, s12 * inv_k},
+                    {s02 * inv_k, s12 * inv_k, s22 * inv_k}};
   double V[3][3];
   jacobi_sym3(C, V);
   int i0 = 0;
