@@ -714,6 +714,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       cudaGraph_t gr = nullptr;
       LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
       set_pdl(true);  // consecutive kernels of the loop overlap their launch with the predecessor's tail
+      const bool fused = mstep_sums_rows(g);
       cudaError_t ce = cudaSuccess;
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
@@ -726,10 +727,13 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
         if (ce == cudaSuccess)
           ce = launch_combine(plan, d, c->xs.p, c->part.p, mode, cfx, c->ls_n.p, c->gam_n.p, c->rows.p, nullptr,
                               s);
-        if (ce == cudaSuccess) ce = launch_final_reduce(plan, d, c->rows.p, c->mom.p, s);
+        // small problems: the M-step kernel sums the combine rows itself (one boundary less)
+        if (ce == cudaSuccess && !fused) ce = launch_final_reduce(plan, d, c->rows.p, c->mom.p, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess) ce = launch_mstep(plan, d, c->mom.p, dp, trace ? c->trace.p : nullptr, iters, s);
+        if (ce == cudaSuccess)
+          ce = launch_mstep(plan, d, fused ? c->rows.p : nullptr, c->mom.p, dp, trace ? c->trace.p : nullptr, iters,
+                            s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
       }
@@ -763,7 +767,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     }
     NvtxRange r("lsgcpd EM loop (graph)");
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * (mode ? 7 : 5);
+    launches += static_cast<int64_t>(iters) * ((mode ? 7 : 5) - (mstep_sums_rows(g) ? 1 : 0));
   }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");

@@ -266,8 +266,14 @@ cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* 
 
 // ----- M step (mstep.cu) -------------------------------------------------------
 // Newton M step of every pair from mom[P][kGlob] and the state update; trace [P][iters][8].
-cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* mom, const DevParams& dp,
+// rows != nullptr: the kernel first sums each pair's combine rows itself (fixed order,
+// FP64) into mom, in place of launch_final_reduce (for plans where mstep_sums_rows holds).
+cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* rows, double* mom, const DevParams& dp,
                          double* trace, int trace_iters, cudaStream_t s);
+// Combine rows per pair small enough for the M-step kernel to sum them (a chain of at most
+// kMaxFusedRows FP64 adds per moment costs less than one more kernel boundary per iteration).
+constexpr int kMaxFusedRows = 32;
+inline bool mstep_sums_rows(const Geo& g) { return g.max_blocks * (g.SB / kCombineSources) <= kMaxFusedRows; }
 // Standalone M step: io[0..75] moments, io[80..91] starting pose (R, t);
 // results R (9), t (3), sigma2, Q, newton steps, damped, halvings at io[96..112].
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s);

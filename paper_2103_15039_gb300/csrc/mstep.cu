@@ -616,12 +616,18 @@ __device__ void newton(Shared& s, int newton_max, double newton_tol) {
 constexpr int kStateWords = static_cast<int>(sizeof(EmState) / sizeof(int));
 static_assert(sizeof(EmState) % sizeof(int) == 0 && kStateWords <= kMThreads, "one word of the state per thread");
 
-__global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ mom_all,
+// rows != nullptr: the pair's combine rows [blk_off[pair] * per_block, blk_off[pair + 1] *
+// per_block) are summed here (in row order, FP64) into mom_all first, in place of the
+// cross-block reduction kernel.
+__global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ rows,
+                                                              const int* __restrict__ blk_off, int per_block,
+                                                              double* __restrict__ mom_all,
                                                               EmState* __restrict__ st_all, DevParams dp,
                                                               double* __restrict__ trace_all, int trace_iters,
                                                               int* __restrict__ done_count, int P) {
   __shared__ Shared s;
   __shared__ EmState es;
+  __shared__ double mom_sh[kGlob];
   __shared__ double nll_sh, pout_sh;
   __shared__ float dmot[12];
   __shared__ int finish_sh, nll_stop_sh;  // written by different lanes in the same phase
@@ -632,6 +638,17 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
   const int pair = blockIdx.x;
   EmState* st = st_all + pair;
   const double* mom = mom_all + static_cast<size_t>(pair) * kGlob;
+  if (rows) {
+    if (tid < kGlob) {
+      const int r0 = blk_off[pair] * per_block, r1 = blk_off[pair + 1] * per_block;
+      double v = 0.0;
+      for (int r = r0; r < r1; ++r) v += rows[static_cast<size_t>(r) * kGlob + tid];
+      mom_sh[tid] = v;
+      mom_all[static_cast<size_t>(pair) * kGlob + tid] = v;
+    }
+    __syncthreads();
+    mom = mom_sh;
+  }
   const int finished = *done_count;
   if (tid < kStateWords) reinterpret_cast<int*>(&es)[tid] = reinterpret_cast<const int*>(st)[tid];
   setup_newton(s, mom, st->R, st->t);
@@ -755,10 +772,10 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
 
 }  // namespace
 
-cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* mom, const DevParams& dp, double* trace,
-                         int trace_iters, cudaStream_t s) {
-  return launch_k(mstep_em_kernel, dim3(p.g.P), dim3(kMThreads), 0, s, mom, d.st, dp, trace, trace_iters,
-                  d.done_count, p.g.P);
+cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* rows, double* mom, const DevParams& dp,
+                         double* trace, int trace_iters, cudaStream_t s) {
+  return launch_k(mstep_em_kernel, dim3(p.g.P), dim3(kMThreads), 0, s, rows, d.tab + p.g.o_blk_off,
+                  p.g.SB / kCombineSources, mom, d.st, dp, trace, trace_iters, d.done_count, p.g.P);
 }
 
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s) {
