@@ -715,10 +715,12 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
       LSG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
       set_pdl(true);  // consecutive kernels of the loop overlap their launch with the predecessor's tail
       const bool fused = mstep_sums_rows(g);
+      const bool fused_prescale = mstep_prescales(g);  // the M step prescales the next E step's records
       cudaError_t ce = cudaSuccess;
       for (int it = 0; it < iters && ce == cudaSuccess; ++it) {
         if (c->timing) ce = cudaEventRecordWithFlags(c->t_iter[4 * it], s, cudaEventRecordExternal);
-        if (ce == cudaSuccess) ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
+        if (ce == cudaSuccess && (it == 0 || !fused_prescale))
+          ce = launch_prescale(plan, d, c->yl.p, mode, c->rec.p, s);
         if (ce == cudaSuccess && mode == 1)
           ce = launch_shift(plan, d, c->xs.p, c->rec.p, cfx, c->part.p, c->status, c->ls_n.p, c->gam_n.p, s);
         if (ce == cudaSuccess) ce = estep_launch(c, plan, d, mode, prec, s);
@@ -733,7 +735,7 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 2], s, cudaEventRecordExternal);
         if (ce == cudaSuccess)
           ce = launch_mstep(plan, d, fused ? c->rows.p : nullptr, c->mom.p, dp, trace ? c->trace.p : nullptr, iters,
-                            s);
+                            fused_prescale && it + 1 < iters ? c->yl.p : nullptr, mode, c->rec.p, s);
         if (ce == cudaSuccess && c->timing)
           ce = cudaEventRecordWithFlags(c->t_iter[4 * it + 3], s, cudaEventRecordExternal);
       }
@@ -767,7 +769,8 @@ lsgcpd_status run_registration(lsgcpd_ctx* c, const float* X, const float* Y, co
     }
     NvtxRange r("lsgcpd EM loop (graph)");
     LSG_CUDA(cudaGraphLaunch(c->gexec, s), "graph launch");
-    launches += static_cast<int64_t>(iters) * ((mode ? 7 : 5) - (mstep_sums_rows(g) ? 1 : 0));
+    launches += static_cast<int64_t>(iters) * ((mode ? 7 : 5) - (mstep_sums_rows(g) ? 1 : 0)) -
+                (mstep_prescales(g) ? iters - 1 : 0);
   }
   if (c->timing) LSG_CUDA(cudaEventRecord(c->t_end, s), "event");
   LSG_CUDA(cudaMemcpyAsync(hs.data(), c->st.p, sizeof(EmState) * P, cudaMemcpyDeviceToHost, s), "copy");

@@ -300,15 +300,7 @@ __global__ void __launch_bounds__(kTile)
   const int tile = blockIdx.x;
   const EmState* sp = st + tab[g.o_tile_pair + tile];
   if (sp->done) return;
-  const long long slot = static_cast<long long>(tile) * kTile + threadIdx.x;
-  const float4 y = yl[slot];
-  const bool pad = y.w == -INFINITY;
-  const float sqc = sp->sqc;
-  float* r = rec + static_cast<size_t>(tile) * kTileFloats + threadIdx.x;
-  r[0 * kTile] = pad ? 0.f : -sqc * y.x;
-  r[1 * kTile] = pad ? 0.f : -sqc * y.y;
-  r[2 * kTile] = pad ? 0.f : -sqc * y.z;
-  r[3 * kTile] = pad ? kPadLambda : (mode ? -y.w : sp->L - y.w);
+  prescale_slot(rec, yl, tile, threadIdx.x, sp->sqc, sp->L, mode);
 }
 
 // ---------------------------------------------------------------------------

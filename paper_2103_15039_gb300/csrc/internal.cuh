@@ -103,6 +103,20 @@ __device__ inline void set_sigma_constants(EmState* st, float s2) {
   st->nll_const = -st->ln_1mw + 1.5 * 0.6931471805599453 * static_cast<double>(lg);
 }
 
+// The sigma-dependent planes 0-3 of record slot `lane` of tile `tile` (y scaled by
+// -sqrt(c), lambda = L - l or -l): written by the prescale kernel, or by the M step of the
+// previous iteration for small problems.
+__device__ inline void prescale_slot(float* rec, const float4* yl, long long tile, int lane, float sqc, float L,
+                                     int mode) {
+  const float4 y = yl[tile * kTile + lane];
+  const bool pad = y.w == -INFINITY;
+  float* r = rec + static_cast<size_t>(tile) * kTileFloats + lane;
+  r[0 * kTile] = pad ? 0.f : -sqc * y.x;
+  r[1 * kTile] = pad ? 0.f : -sqc * y.y;
+  r[2 * kTile] = pad ? 0.f : -sqc * y.z;
+  r[3 * kTile] = pad ? kPadLambda : (mode ? -y.w : L - y.w);
+}
+
 // E-step constants for the current (R, t, sigma2) of the state.
 __device__ inline void set_estep_constants(EmState* st) {
   for (int i = 0; i < 9; ++i) st->Rf[i] = static_cast<float>(st->R[i]);
@@ -268,12 +282,18 @@ cudaError_t launch_final_reduce(const BatchPlan& p, const Dev& d, const double* 
 // Newton M step of every pair from mom[P][kGlob] and the state update; trace [P][iters][8].
 // rows != nullptr: the kernel first sums each pair's combine rows itself (fixed order,
 // FP64) into mom, in place of launch_final_reduce (for plans where mstep_sums_rows holds).
+// yl != nullptr: the kernel also writes the next E step's sigma-dependent record planes
+// (in place of launch_prescale; for plans where mstep_prescales holds).
 cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* rows, double* mom, const DevParams& dp,
-                         double* trace, int trace_iters, cudaStream_t s);
+                         double* trace, int trace_iters, const float4* yl, int mode, float* rec, cudaStream_t s);
 // Combine rows per pair small enough for the M-step kernel to sum them (a chain of at most
 // kMaxFusedRows FP64 adds per moment costs less than one more kernel boundary per iteration).
 constexpr int kMaxFusedRows = 32;
 inline bool mstep_sums_rows(const Geo& g) { return g.max_blocks * (g.SB / kCombineSources) <= kMaxFusedRows; }
+// Target tiles per pair small enough for the M-step CTA (one thread per slot) to prescale
+// faster than a separate launch (measured: ahead at 8 tiles, behind at 32).
+constexpr int kMaxFusedTiles = 16;
+inline bool mstep_prescales(const Geo& g) { return mstep_sums_rows(g) && g.max_tiles <= kMaxFusedTiles; }
 // Standalone M step: io[0..75] moments, io[80..91] starting pose (R, t);
 // results R (9), t (3), sigma2, Q, newton steps, damped, halvings at io[96..112].
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s);

@@ -619,12 +619,19 @@ static_assert(sizeof(EmState) % sizeof(int) == 0 && kStateWords <= kMThreads, "o
 // rows != nullptr: the pair's combine rows [blk_off[pair] * per_block, blk_off[pair + 1] *
 // per_block) are summed here (in row order, FP64) into mom_all first, in place of the
 // cross-block reduction kernel.
+// yl != nullptr: the epilogue also writes the sigma-dependent record planes of the pair's
+// tiles [tile_off[pair], tile_off[pair + 1]) for the next E step (one thread per slot), in
+// place of the prescale kernel.
+static_assert(kMThreads == kTile, "one thread per record slot");
 __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __restrict__ rows,
                                                               const int* __restrict__ blk_off, int per_block,
                                                               double* __restrict__ mom_all,
                                                               EmState* __restrict__ st_all, DevParams dp,
                                                               double* __restrict__ trace_all, int trace_iters,
-                                                              int* __restrict__ done_count, int P) {
+                                                              int* __restrict__ done_count, int P,
+                                                              const float4* __restrict__ yl,
+                                                              const int* __restrict__ tile_off, int mode,
+                                                              float* __restrict__ rec) {
   __shared__ Shared s;
   __shared__ EmState es;
   __shared__ double mom_sh[kGlob];
@@ -723,6 +730,8 @@ __global__ void __launch_bounds__(kMThreads) mstep_em_kernel(const double* __res
     }
   }
   __syncthreads();
+  if (yl && !es.done)
+    for (int t = tile_off[pair]; t < tile_off[pair + 1]; ++t) prescale_slot(rec, yl, t, tid, es.sqc, es.L, mode);
   if (tid < kStateWords) reinterpret_cast<int*>(st)[tid] = reinterpret_cast<const int*>(&es)[tid];
 }
 
@@ -773,9 +782,10 @@ __global__ void constants_kernel(EmState* st, double sigma2, double w, double V,
 }  // namespace
 
 cudaError_t launch_mstep(const BatchPlan& p, const Dev& d, const double* rows, double* mom, const DevParams& dp,
-                         double* trace, int trace_iters, cudaStream_t s) {
+                         double* trace, int trace_iters, const float4* yl, int mode, float* rec, cudaStream_t s) {
   return launch_k(mstep_em_kernel, dim3(p.g.P), dim3(kMThreads), 0, s, rows, d.tab + p.g.o_blk_off,
-                  p.g.SB / kCombineSources, mom, d.st, dp, trace, trace_iters, d.done_count, p.g.P);
+                  p.g.SB / kCombineSources, mom, d.st, dp, trace, trace_iters, d.done_count, p.g.P, yl,
+                  d.tab + p.g.o_tile_off, mode, rec);
 }
 
 cudaError_t launch_mstep_standalone(double* io, const DevParams& dp, cudaStream_t s) {
